@@ -1,0 +1,395 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks.  None of them retypes the oracle's
+formulas: they check identities between the paper's equations, invariants,
+closed-form solutions and textbook lattice properties, chosen so that a
+dropped term, a wrong sign or index or a transposed operand in the oracle
+fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, OracleParams, lattice_tables
+from oracle.ltne_oracle import BC_CAVITY, BC_CHANNEL, BC_PERIODIC
+
+
+def _e():
+    e, w, M, Mi, N, Ni = lattice_tables()
+    return e[0], e[1], w, M, Mi, N, Ni
+
+
+# ---------------------------------------------------------------- p1 -----
+def test_velocity_set_and_weights_are_isotropic():
+    """Eq. 8 and the weights below Eq. 24: the D2Q9 set must reproduce the
+    isotropic lattice tensors up to fourth order with cs^2 = 1/3."""
+    ex, ey, w, *_ = _e()
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    E = np.stack([ex, ey])
+    assert np.allclose(E @ w, 0, atol=1e-15)
+    T2 = np.einsum("i,ai,bi->ab", w, E, E)
+    assert np.allclose(T2, np.eye(2) / 3, atol=1e-15)
+    T3 = np.einsum("i,ai,bi,ci->abc", w, E, E, E)
+    assert np.allclose(T3, 0, atol=1e-15)
+    T4 = np.einsum("i,ai,bi,ci,di->abcd", w, E, E, E, E)
+    d = np.eye(2)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+           + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(T4, iso, atol=1e-15)
+    # opposite pairs exist for every moving direction
+    for i in range(1, 9):
+        assert sum((ex[j] == -ex[i]) and (ey[j] == -ey[i]) for j in range(9)) == 1
+
+
+def test_moment_matrices_match_their_definitions():
+    """Eq. 13 rows are the moments named in Eq. 14 (rho, e, epsilon, j, q,
+    p_xx, p_xy, as polynomials of e_i); Eq. 36 rows are [1, e_x, e_y,
+    5e^2-4, e_x^2-e_y^2] as the paper defines them above the table."""
+    ex, ey, w, M, Mi, N, Ni = _e()
+    e2 = ex ** 2 + ey ** 2
+    rows = np.array([
+        np.ones(9), 3 * e2 - 4, (9 * e2 ** 2 - 21 * e2 + 8) / 2,
+        ex, (3 * e2 - 5) * ex, ey, (3 * e2 - 5) * ey, ex ** 2 - ey ** 2, ex * ey])
+    assert np.array_equal(M, rows)
+    ex5, ey5 = ex[:5], ey[:5]
+    e25 = ex5 ** 2 + ey5 ** 2
+    rowsN = np.array([np.ones(5), ex5, ey5, 5 * e25 - 4, ex5 ** 2 - ey5 ** 2])
+    assert np.array_equal(N, rowsN)
+
+
+def test_moment_matrices_orthogonal_and_inverses():
+    """M M^T = diag(9,36,36,6,12,6,12,4,4); N N^T = diag(5,2,2,20,4) (both
+    exact in integers); the numerically formed inverses invert them."""
+    ex, ey, w, M, Mi, N, Ni = _e()
+    assert np.array_equal(M @ M.T, np.diag([9, 36, 36, 6, 12, 6, 12, 4, 4]).astype(float))
+    assert np.array_equal(N @ N.T, np.diag([5, 2, 2, 20, 4]).astype(float))
+    assert np.allclose(Mi @ M, np.eye(9), atol=1e-14)
+    assert np.allclose(Ni @ N, np.eye(5), atol=1e-14)
+
+
+# ---------------------------------------------------------------- p2 -----
+def _box(nx=8, ny=8, **kw):
+    return Oracle(OracleParams.make(nx, ny, **kw))
+
+
+def test_equilibrium_moments_consistent():
+    """Eq. 15 equals M times Eq. 24; Eq. 37 equals N times Eq. 50; Eq. 38
+    equals N times Eq. 51, including the (-4 + 5 varpi) T entry."""
+    rng = np.random.default_rng(11)
+    ex, ey, w, M, Mi, N, Ni = _e()
+    for varpi in (0.4, 0.7):
+        o = _box(varpi=varpi)
+        for _ in range(20):
+            rho, ux, uy = rng.uniform(0.8, 1.2), rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)
+            Tf, Ts, phi = rng.uniform(-1, 2), rng.uniform(-1, 2), rng.uniform(0.3, 0.95)
+            fe, gfe, gse, me, _ = o.equilibria(rho, ux, uy, Tf, Ts, phi)
+            assert np.allclose(M @ fe, me, atol=1e-15, rtol=0)
+            nfeq = np.array([Tf, ux * Tf / phi, uy * Tf / phi, (-4 + 5 * varpi) * Tf, 0])
+            nseq = np.array([Ts, 0, 0, (-4 + 5 * varpi) * Ts, 0])
+            assert np.allclose(N @ gfe, nfeq, atol=1e-14, rtol=0)
+            assert np.allclose(N @ gse, nseq, atol=1e-14, rtol=0)
+            # f^eq carries exactly the mass, momentum and the porous
+            # momentum flux rho cs^2 I + rho u u / phi of Sec. 3.1.
+            E = np.stack([ex, ey])
+            assert fe.sum() == pytest.approx(rho, abs=1e-15)
+            assert np.allclose(E @ fe, rho * np.array([ux, uy]), atol=1e-15)
+            Pi = np.einsum("i,ai,bi->ab", fe, E, E)
+            u = np.array([ux, uy])
+            assert np.allclose(Pi, rho / 3 * np.eye(2) + rho * np.outer(u, u) / phi, atol=1e-15)
+
+
+# ---------------------------------------------------------------- p3 -----
+def test_forcing_moments():
+    """The velocity-space forcing used for Eq. 16 (reading of a garbled
+    equation) must carry zero mass, momentum rho F and second moment
+    rho (uF + Fu)/phi, and M S must equal the closed form
+    (0, 6 rho u.F/phi, -6 rho u.F/phi, rho Fx, -rho Fx, rho Fy, -rho Fy,
+    2 rho (ux Fx - uy Fy)/phi, rho (ux Fy + uy Fx)/phi)."""
+    rng = np.random.default_rng(12)
+    ex, ey, w, M, Mi, N, Ni = _e()
+    E = np.stack([ex, ey])
+    o = _box()
+    for _ in range(20):
+        rho, ux, uy = rng.uniform(0.8, 1.2), rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)
+        Fx, Fy, phi = rng.uniform(-1e-3, 1e-3), rng.uniform(-1e-3, 1e-3), rng.uniform(0.3, 0.95)
+        *_, S = o.equilibria(rho, ux, uy, 0.5, 0.5, phi, Fx, Fy)
+        u, F = np.array([ux, uy]), np.array([Fx, Fy])
+        assert abs(S.sum()) < 1e-18
+        assert np.allclose(E @ S, rho * F, atol=1e-18, rtol=1e-13)
+        P = np.einsum("i,ai,bi->ab", S, E, E)
+        assert np.allclose(P, rho * (np.outer(u, F) + np.outer(F, u)) / phi, atol=1e-18, rtol=1e-12)
+        uF = u @ F
+        closed = np.array([0, 6 * rho * uF / phi, -6 * rho * uF / phi, rho * Fx, -rho * Fx,
+                           rho * Fy, -rho * Fy, 2 * rho * (ux * Fx - uy * Fy) / phi,
+                           rho * (ux * Fy + uy * Fx) / phi])
+        assert np.allclose(M @ S, closed, atol=1e-18, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- p4 -----
+def test_velocity_solve_satisfies_implicit_definition():
+    """Eq. 20 with Eqs. 21-22 must solve Eq. 19 with the force of Eq. 5,
+    and the temperatures of Eqs. 43-44 must solve Eqs. 41-42."""
+    rng = np.random.default_rng(13)
+    ex, ey, w, *_ = _e()
+    E = np.stack([ex, ey])
+    for trial in range(30):
+        phi = rng.uniform(0.3, 0.9)
+        kw = dict(porosity=phi, Da=10 ** rng.uniform(-4, -1), H=10 ** rng.uniform(-1, 3),
+                  Ra=10 ** rng.uniform(3, 6), gamma_sf=10 ** rng.uniform(-1, 2),
+                  sigma=rng.uniform(0.5, 2), qf=rng.uniform(-1e-4, 1e-4),
+                  qs=rng.uniform(-1e-4, 1e-4), ext_ax=rng.uniform(-1e-4, 1e-4))
+        o = _box(16, 16, **kw)
+        d = o.derived()
+        K, Fphi = o.medium()
+        K, Fphi = K[0, 0], Fphi[0, 0]
+        f = w * rng.uniform(0.9, 1.1, 9)
+        gf = rng.uniform(0.0, 0.3, 5)
+        gs = rng.uniform(0.0, 0.3, 5)
+        _, _, _, m, _, _ = o.node(0, f, gf, gs)
+        u = np.array([m["ux"], m["uy"]])
+        G = np.array([m["Gx"], m["Gy"]])
+        umag = np.hypot(*u)
+        Fvec = -phi * d["nu_f"] / K * u - phi * Fphi / np.sqrt(K) * umag * u + phi * G
+        assert np.allclose([m["Fx"], m["Fy"]], Fvec, rtol=1e-13, atol=1e-20)
+        lhs = m["rho"] * u
+        rhs = E @ f + 0.5 * m["rho"] * Fvec
+        assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-17)
+        # Eq. 41 with Eq. 42 (a, b are the per-node exchange coefficients)
+        Srf = m["a"] * (m["Ts"] - m["Tf"]) + kw["qf"]
+        Srs = m["b"] * (m["Tf"] - m["Ts"]) + kw["qs"]
+        assert m["Tf"] == pytest.approx(gf.sum() + 0.5 * Srf, rel=1e-13, abs=1e-15)
+        assert m["Ts"] == pytest.approx(gs.sum() + 0.5 * Srs, rel=1e-13, abs=1e-15)
+        # buoyancy is along +y for T_f above T_0 (reading: gravity along -y)
+        assert m["Gy"] == pytest.approx(d["gbeta"] * (m["Tf"] - 0.5), rel=1e-13, abs=1e-20)
+
+
+def test_parameter_mapping_reproduces_dimensionless_groups():
+    """The lattice values recover the groups of Sec. 2 (Ra, Pr, Da, J_e,
+    gamma_sf / sigma) and the transport relations of Eqs. 23 and 49."""
+    o = _box(33, 65, Ra=3e5, Pr=0.7, J_e=1.3, gamma_sf=7.0, sigma=2.0, H=40.0)
+    d = o.derived()
+    L = 64.0
+    assert d["L"] == L
+    Ra = d["gbeta"] * 1.0 * L ** 3 / (d["nu_f"] * d["alpha_f"])
+    assert Ra == pytest.approx(3e5, rel=1e-12)
+    assert d["nu_f"] / d["alpha_f"] == pytest.approx(0.7, rel=1e-14)
+    assert d["nu_e"] / d["nu_f"] == pytest.approx(1.3, rel=1e-14)
+    assert d["alpha_s"] / d["alpha_f"] == pytest.approx(7.0 / 2.0, rel=1e-14)
+    assert d["cs2"] * (1 / d["s_nu"] - 0.5) == pytest.approx(d["nu_e"], rel=1e-13)
+    assert d["csT2"] * (1 / d["zeta_alpha"] - 0.5) == pytest.approx(d["alpha_f"], rel=1e-13)
+    assert d["csT2"] * (1 / d["eta_alpha"] - 0.5) == pytest.approx(d["alpha_s"], rel=1e-13)
+    # H_v = h_v L^2 / k_f  =>  h_v / (rho c)_f = H alpha_f / L^2
+    assert d["hv_over_rhoc_f"] * L ** 2 / d["alpha_f"] == pytest.approx(40.0, rel=1e-13)
+
+
+def test_ergun_medium():
+    """Eq. 7 per node; with the particle diameter fixed from the mean
+    Darcy number, the mean of K / L^2 over the nodes equals Da."""
+    rng = np.random.default_rng(14)
+    phi = rng.uniform(0.3, 0.9, size=(20, 24))
+    o = Oracle(OracleParams.make(24, 20, ergun_K=1, Da=1e-3), phi=phi)
+    K, F = o.medium()
+    L = 19.0
+    assert (K / L ** 2).mean() == pytest.approx(1e-3, rel=1e-12)
+    # ratios between nodes follow phi^3 / (1 - phi)^2, independent of d
+    r = (phi ** 3 / (1 - phi) ** 2)
+    assert np.allclose(K / K[0, 0], r / r[0, 0], rtol=1e-12)
+    assert np.allclose(F ** 2 * 150 * phi ** 3, 1.75 ** 2, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- p5 -----
+def test_conservation_periodic():
+    """Periodic box, uniform porosity, no internal generation: total mass
+    and total energy sum[phi sum g_f + (1-phi) sigma sum g_s] are conserved
+    because the interphase sources cancel (the remark after Eq. 42)."""
+    rng = np.random.default_rng(15)
+    nx = ny = 16
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=1e5, H=50.0, gamma_sf=5.0,
+                                 sigma=1.7, porosity=0.45))
+    o.init(rho=1 + 0.01 * rng.standard_normal(nx * ny), ux=0.02 * rng.standard_normal(nx * ny),
+           uy=0.02 * rng.standard_normal(nx * ny), Tf=rng.uniform(0, 1, nx * ny),
+           Ts=rng.uniform(0, 1, nx * ny))
+    ob0 = o.observables()
+    o.step(2000)
+    ob1 = o.observables()
+    # round-off only: at most a few ulp of drift per step
+    tol = 2000 * 4 * np.finfo(float).eps
+    assert ob1["mass"] == pytest.approx(ob0["mass"], rel=tol)
+    assert ob1["energy"] == pytest.approx(ob0["energy"], rel=tol)
+    # and the run did something
+    assert ob1["max_dT"] < 0.5 * ob0["max_dT"]
+
+
+# ---------------------------------------------------------------- p6 -----
+@pytest.mark.parametrize("H,phi,sigma,gsf", [(200.0, 0.6, 1.0, 1.0), (5e3, 0.35, 2.5, 30.0)])
+def test_interphase_relaxation_trapezoid_law(H, phi, sigma, gsf):
+    """Uniform fields with T_f != T_s: Eqs. 41-46 with the (I - Q/2) source
+    treatment of Eqs. 32-33 advance the difference by the trapezoid rule,
+    D^{n+1} = D^n (1 - k/2)/(1 + k/2) with k = a + b, to round-off, while
+    phi T_f + (1 - phi) sigma T_s stays fixed."""
+    nx = ny = 4
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=1e4, H=H, porosity=phi,
+                                 sigma=sigma, gamma_sf=gsf))
+    o.init(Tf=np.full(nx * ny, 0.9), Ts=np.full(nx * ny, 0.1))
+    mac = o.macros()
+    _, _, _, m, _, _ = o.node(0, *[x[0, 0] for x in o.get_pops()])
+    k = m["a"] + m["b"]
+    r = (1 - k / 2) / (1 + k / 2)
+    D0 = mac["Tf"][0, 0] - mac["Ts"][0, 0]
+    W0 = phi * mac["Tf"][0, 0] + (1 - phi) * sigma * mac["Ts"][0, 0]
+    for n in range(1, 40):
+        o.step(1)
+        mac = o.macros()
+        D = mac["Tf"] - mac["Ts"]
+        assert np.allclose(D, D0 * r ** n, rtol=1e-12, atol=1e-15)
+        W = phi * mac["Tf"] + (1 - phi) * sigma * mac["Ts"]
+        assert np.allclose(W, W0, rtol=1e-14)
+    # the continuous law exp(-k t) is matched to the trapezoid rule's O(k^3)
+    assert abs(np.log(abs(r)) + k) <= k ** 3 / 12 * 1.01 + 1e-15
+
+
+# ---------------------------------------------------------------- p7/p8 --
+def test_uniform_forchheimer_flow():
+    """Uniform periodic flow under a constant body acceleration A: the
+    momentum grows by rho F per step, i.e. rho u^{n+1} - rho F(u^{n+1})/2 =
+    rho u^n + rho F(u^n)/2 with F from Eq. 5, and u tends to the root of
+    nu/K u + F_phi/sqrt(K) u^2 = A."""
+    nx = ny = 4
+    A = 2e-4
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=0.0, nu_override=0.05, Da=1e-3,
+                                 porosity=0.5, ext_ax=A, T_hot=0.5, T_cold=0.5))
+    o.init()
+    K, Fp = o.medium()
+    K, Fp = K[0, 0], Fp[0, 0]
+    nu, phi = 0.05, 0.5
+
+    def F(u):
+        return -phi * nu / K * u - phi * Fp / np.sqrt(K) * abs(u) * u + phi * A
+
+    u_prev = o.macros()["ux"][0, 0]
+    rho = o.macros()["rho"][0, 0]
+    for _ in range(200):
+        o.step(1)
+        mac = o.macros()
+        u = mac["ux"][0, 0]
+        assert np.allclose(mac["ux"], u, rtol=0, atol=1e-17)
+        assert np.allclose(mac["uy"], 0, atol=1e-17)
+        assert rho * u - 0.5 * rho * F(u) == pytest.approx(rho * u_prev + 0.5 * rho * F(u_prev),
+                                                           rel=1e-12, abs=1e-18)
+        u_prev = u
+    o.step(20000)
+    u = o.macros()["ux"][0, 0]
+    a, b = nu / K, Fp / np.sqrt(K)
+    u_inf = (-a + np.sqrt(a * a + 4 * b * A)) / (2 * b)
+    assert u == pytest.approx(u_inf, rel=1e-10)
+
+
+# ---------------------------------------------------------------- p9 -----
+def test_cavity_centro_symmetry():
+    """Uniform porosity, walls at +1 / -1 and T_0 = 0: the cavity of Sec. 4
+    is symmetric under the half-turn x -> L - x, y -> L - y, which maps T to
+    -T and u to -u, at every step.  (With T_0 != 0 the advective part
+    (e_i.u) T_0 / (2 phi) of Eq. 50 is even under the half-turn, so the
+    weakly compressible flow breaks the symmetry at O(Ma^2); every term is
+    odd in T only when T_0 = 0.)"""
+    nx, ny = 24, 24
+    o = Oracle(OracleParams.make(nx, ny, Ra=1e5, H=20.0, gamma_sf=3.0, T_hot=1.0, T_cold=-1.0,
+                                 T_ref=0.0))
+    o.init()
+    for _ in range(4):
+        o.step(150)
+        m = o.macros()
+        for k in ("Tf", "Ts", "ux", "uy"):
+            assert np.allclose(m[k], -m[k][::-1, ::-1], rtol=0, atol=1e-13)
+        assert np.abs(m["ux"]).max() > 1e-4
+        assert np.allclose(m["rho"], m["rho"][::-1, ::-1], rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- p10 ----
+def _brinkman(ny):
+    nu, nu_e_ratio, phi, Da, A = 0.1, 1.5, 0.6, 5e-3, 1e-6
+    o = Oracle(OracleParams.make(4, ny, bc=BC_CHANNEL, Ra=0.0, nu_override=nu, J_e=nu_e_ratio,
+                                 porosity=phi, Da=Da, F_phi=0.0, ext_ax=A, T_hot=0.5,
+                                 T_cold=0.5))
+    o.init()
+    K = o.medium()[0][0, 0]
+    L = ny - 1.0
+    o.step(int(40 * K / (phi * nu)) + 4 * int(L * L / (nu * nu_e_ratio)))
+    ux = o.macros()["ux"][:, 1]
+    y = np.arange(ny)
+    r = np.sqrt(phi * nu / (K * nu * nu_e_ratio))
+    ua = A * K / nu * (1 - np.cosh(r * (y - L / 2)) / np.cosh(r * L / 2))
+    return np.linalg.norm(ux - ua) / np.linalg.norm(ua)
+
+
+@pytest.mark.slow
+def test_brinkman_channel_profile():
+    """Steady channel flow with the Forchheimer term off obeys the Brinkman
+    equation nu_e u'' - phi nu_f u / K + phi A = 0 (Eqs. 2, 5), whose
+    solution is a cosh profile; the error falls at about second order."""
+    errs = [_brinkman(ny) for ny in (17, 33, 65)]
+    assert errs[2] <= 1e-3
+    order = np.log2(errs[1] / errs[2])
+    assert order > 1.6, errs
+
+
+# ---------------------------------------------------------------- p11 ----
+def test_pure_conduction_walls_and_nusselt():
+    """Ra = 0: steady conduction between the isothermal walls is linear in
+    x for both phases and Nu = 1 on both walls, which checks the wall
+    rebuild and the wall-flux stencil."""
+    nx = ny = 16
+    o = Oracle(OracleParams.make(nx, ny, Ra=0.0, nu_override=0.2, H=30.0, gamma_sf=4.0,
+                                 sigma=1.5, T_hot=1.0, T_cold=0.0))
+    o.init()
+    o.step(12000)
+    ob = o.observables()
+    for k in ("Nu_f_hot", "Nu_s_hot", "Nu_f_cold", "Nu_s_cold"):
+        assert ob[k] == pytest.approx(1.0, abs=1e-10)
+    m = o.macros()
+    x = np.arange(nx)
+    lin = 1.0 - x / (nx - 1.0)
+    for k in ("Tf", "Ts"):
+        assert np.allclose(m[k][1:-1, :], lin[None, :], atol=1e-10)
+    assert np.abs(m["ux"]).max() == 0 and np.abs(m["uy"]).max() == 0
+
+
+# ---------------------------------------------------------------- p12 ----
+@pytest.mark.slow
+def test_lte_limit():
+    """Large interphase coefficient drives T_f -> T_s (local thermal
+    equilibrium); the gap shrinks roughly as 1/H."""
+    gaps, fields = [], []
+    for H in (1e2, 1e4, 1e6):
+        o = Oracle(OracleParams.make(32, 32, Ra=1e4, H=H, gamma_sf=10.0))
+        o.init().step(3000)
+        gaps.append(o.observables()["max_dT"])
+        fields.append(o.macros()["Tf"])
+    assert gaps[0] > gaps[1] > gaps[2]
+    for a, b in zip(gaps, gaps[1:]):
+        assert 30 < a / b < 300
+    assert np.abs(fields[1] - fields[2]).max() < np.abs(fields[0] - fields[2]).max()
+
+
+# ---------------------------------------------------------------- p13 ----
+def test_solid_diffusivity_chapman_enskog():
+    """A sine mode of T_s with u = 0 and H = 0 decays at alpha_s k^2 with
+    alpha_s = c_sT^2 (1/eta_alpha - 1/2) (Eq. 49, c_sT^2 = varpi/2)."""
+    nx, ny = 128, 3
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=0.0, nu_override=0.1, H=0.0,
+                                 gamma_sf=3.0, sigma=1.0))
+    d = o.derived()
+    x = np.arange(nx)
+    k = 2 * np.pi / nx
+    Ts = 0.5 + 0.1 * np.sin(k * x)
+    o.init(Ts=np.tile(Ts, ny))
+
+    def amp():
+        t = o.macros()["Ts"][1]
+        return 2 * np.mean((t - 0.5) * np.sin(k * x))
+
+    o.step(200)
+    a1 = amp()
+    o.step(1800)
+    a2 = amp()
+    rate = -np.log(a2 / a1) / 1800
+    assert rate == pytest.approx(d["alpha_s"] * k * k, rel=1e-3)
