@@ -1,0 +1,341 @@
+"""Throughput benchmark of the fused three-distribution MRT-LB step.
+
+Default workload: the differentially heated porous cavity at 4096 x 4096
+nodes, FP32 storage, per-node porosity U[0.3, 0.9] (seed 2) with the Ergun
+medium at mean Da = 1e-3, Ra = 1e6, H = 100, conductivity ratio 10
+(synthetic inputs).  A "step" is one lattice time step of all nodes: the
+D2Q9 flow and both D2Q5 temperature distributions, collision, streaming and
+walls.  MLUPS = nodes x steps / seconds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
+cavity (independent replicas, weak scaling) and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1608_04118_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MLUPS (all 3 distributions fused)"
+UNIT = "MLUPS"
+# Algorithmic bytes per lattice update: read + write of 19 populations plus
+# the per-node porosity read.
+BYTES_PER_LUP = {"f32": 2 * 19 * 4 + 4, "f64": 2 * 19 * 8 + 8, "f16": 2 * 19 * 2 + 4,
+                 "bf16": 2 * 19 * 2 + 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=500)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096, help="cavity side (nodes)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(n, storage):
+    c = W.C2_THROUGHPUT
+    return {"workload": "porous LTNE cavity %dx%d, per-node porosity U[%.1f,%.1f] seed %d, "
+                        "Ergun K (mean Da %.0e), Ra %.0e, H %.0f, gamma_sf %.0f"
+                        % (n, n, c["phi_lo"], c["phi_hi"], c["seed"], c["Da"], c["Ra"], c["H"],
+                           c["gamma_sf"]),
+            "nx": n, "ny": n, "storage": storage, "lattice": "D2Q9 + 2 x D2Q5 (MRT)",
+            "l2": "inputs larger than L2 (%.2f GB of populations per buffer)"
+                  % (19 * BYTES_PER_LUP[storage] / 38 * n * n / 1e9 if storage != "f64"
+                     else 19 * 8 * n * n / 1e9)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(storage, n):
+    """ncu DRAM bytes per launch of the step kernel from the committed
+    profile summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        from paper_1608_04118_gb300 import build as B
+
+        if d.get("source_hash") != B.kernel_source_hash():
+            return None
+        e = d["entries"].get(storage)
+        if not e:
+            return None
+        # traffic grows with the node count; scale the captured case
+        return float(e["dram_bytes_per_launch"]) * (n * n) / float(e["nodes"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_oracle(n, target_s=12.0):
+    """The FP64 oracle on the host cores, on a bounded sample of the
+    workload: the same cavity physics on a 1024 x 1024 lattice for as many
+    steps as fit in about target_s seconds."""
+    import oracle
+    from oracle import Oracle, OracleParams
+
+    c = W.C2_THROUGHPUT
+    m = min(n, 1024)
+    phi = W.porosity_field(m, m, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+    p = OracleParams.make(m, m, ergun_K=1, Ra=c["Ra"], Pr=c["Pr"], Da=c["Da"], H=c["H"],
+                          gamma_sf=c["gamma_sf"], sigma=c["sigma"], T_hot=c["T_hot"],
+                          T_cold=c["T_cold"], T_ref=c["T_ref"])
+    o = Oracle(p, phi=phi).init()
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    k = max(1, int(target_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    return {"value": m * m * k / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "FP64 oracle, %dx%d cavity with the same physics, %d steps (%.1f s)"
+                      % (m, m, k, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, as it stands, on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from oracle import Oracle, OracleParams
+
+    oracle.build()
+    c = W.C2_THROUGHPUT
+    m = min(args.n, 512)  # bounded sample per step so that the run ends in minutes
+    phi = W.porosity_field(m, m, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+    p = OracleParams.make(m, m, ergun_K=1, Ra=c["Ra"], Pr=c["Pr"], Da=c["Da"], H=c["H"],
+                          gamma_sf=c["gamma_sf"], sigma=c["sigma"], T_hot=c["T_hot"],
+                          T_cold=c["T_cold"], T_ref=c["T_ref"])
+    o = Oracle(p, phi=phi).init()
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = m * m * args.steps / dt / 1e6
+    sample = ("FP64 oracle on a %dx%d cavity with the same physics per step (bounded sample "
+              "of the %dx%d workload)" % (m, m, args.n, args.n))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.n, args.storage),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1608_04118_gb300 import build as B
+
+    B.build()
+    from paper_1608_04118_gb300.ltne import Cavity, LTNE_K_ERGUN
+
+    c = W.C2_THROUGHPUT
+    n = args.n
+    phi = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], c["seed"] + rank).reshape(-1)
+    kw = dict(Ra=c["Ra"], Pr=c["Pr"], Da=c["Da"], H=c["H"], gamma_sf=c["gamma_sf"],
+              sigma=c["sigma"], T_hot=c["T_hot"], T_cold=c["T_cold"], T_ref=c["T_ref"])
+    stream = torch.cuda.Stream(dev)
+    cav = Cavity(n, n, stream=stream, storage=args.storage, permeability=LTNE_K_ERGUN,
+                 porosity_field=1, **kw)
+    cav.set_fields(porosity=phi)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput ----
+    with torch.cuda.stream(stream):
+        cav.step(max(args.warmup, 3))
+    barrier()
+    sampler = None if args.no_clocks else ClockSampler(local)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    launches0 = cav.launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    cav.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    t = ev0.elapsed_time(ev1) / 1e3
+    launches = cav.launches - launches0
+    t_max = t
+    if ws > 1:
+        tt = torch.tensor([t], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    nodes = n * n
+    value = ws * nodes * args.steps / t_max / 1e6
+    per_launch = t / args.steps
+    peak, peak_kind = load_peaks()
+    achieved = BYTES_PER_LUP[args.storage] * nodes / per_launch / 1e9
+    ob = cav.observables()
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        k = args.steps
+        host_out = {}
+        barrier()
+        t0 = time.perf_counter()
+        cav.set_fields(porosity=phi)  # H2D of the porosity and the initial fields
+        cav.step(k)
+        host_out = cav.fields()       # D2H of the fields
+        host_ob = cav.observables()   # D2H of the observables
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        tt = te
+        if ws > 1:
+            tq = torch.tensor([te], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(tq, op=torch.distributed.ReduceOp.MAX)
+            tt = float(tq.item())
+        h2d = phi.nbytes + 5 * nodes * 4  # porosity + five staged fields (compute type)
+        d2h = 5 * nodes * 4 + 17 * 8
+        e2e = {"value": ws * nodes * k / tt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / k, "d2h_bytes_per_step": d2h / k,
+               "note": "whole run through the C ABI: set_fields from host arrays, %d steps, "
+                       "get_fields + observables to host" % k}
+        assert host_ob["nonfinite"] == 0 and np.isfinite(host_out["Tf"]).all()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline_oracle(n)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.storage == "f64" else "f32", "storage": args.storage,
+        "data": "synthetic", "config": workload_config(n, args.storage),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "frac_of_8TBs": achieved / 8000.0,
+                     "bytes_per_lup": BYTES_PER_LUP[args.storage],
+                     "traffic": kernel_traffic(args.storage, n),
+                     "kernel": "k_step<%s> (one launch = one step of %d nodes)" % (args.storage,
+                                                                                    nodes)},
+        "gpu_launches": int(launches),
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+        "observables": {"Nu_f_hot": ob["Nu_f_hot"], "Nu_s_hot": ob["Nu_s_hot"],
+                        "nonfinite": ob["nonfinite"], "step": ob["step"]},
+    }
+    if ws > 1:
+        line["config"]["parallelism"] = "replicas x%d (independent cavities)" % ws
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

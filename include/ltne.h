@@ -1,0 +1,194 @@
+/*
+ * ltne.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * three-distribution MRT lattice Boltzmann time step of Liu & He,
+ * "Multiple-relaxation-time lattice Boltzmann model for convection heat
+ * transfer in porous media under local thermal non-equilibrium condition"
+ * (arXiv:1608.04118).
+ *
+ * One time step advances, in one fused pass per lattice node,
+ *   - the D2Q9 density distribution f of the generalized non-Darcy
+ *     (Brinkman-Forchheimer) flow: Sec. 3.1, Eqs. 9-24;
+ *   - the D2Q5 fluid-phase and solid-phase temperature distributions g_f,
+ *     g_s with the interphase source terms and their (I - Q/2) treatment:
+ *     Sec. 3.2, Eqs. 27-51;
+ *   - the wall rebuild of the cavity of Sec. 4 (non-equilibrium
+ *     extrapolation, which the paper cites but does not define: every
+ *     population of a wall node is replaced after streaming by the
+ *     equilibrium at the wall values plus the non-equilibrium part of the
+ *     interior neighbour; corners use the diagonal neighbour and belong to
+ *     the isothermal walls; adiabatic rows take the neighbour's temperature).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an int status (LTNE_OK or an LTNE_ERR_* code) and
+ *     never aborts; ltne_error_string() names the code.
+ *   - Host arrays are row-major [ny][nx] doubles: x is horizontal (hot wall
+ *     at x = 0, cold wall at x = nx-1), y is vertical (gravity along -y).
+ *   - The caller owns all memory.  Device memory is one workspace buffer
+ *     the caller allocates (e.g. a torch tensor) and binds with
+ *     ltne_bind_workspace(); the handle holds only host-side metadata and
+ *     the CUDA graphs it builds.  The library allocates no device memory.
+ *   - All device work is enqueued on the stream given to ltne_create().
+ *     Calls that return host data synchronise that stream.
+ *   - A handle is not thread-safe; use one handle per stream.
+ */
+#ifndef LTNE_H
+#define LTNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+  LTNE_OK = 0,
+  LTNE_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter value        */
+  LTNE_ERR_UNSTABLE_TAU = 2,  /* a relaxation rate falls outside (0, 2)       */
+  LTNE_ERR_CUDA = 3,          /* a CUDA runtime call failed                   */
+  LTNE_ERR_NONFINITE = 4,     /* observables found NaN/Inf in the fields      */
+  LTNE_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up           */
+  LTNE_ERR_STATE = 6,         /* call out of order (e.g. no workspace bound)  */
+  LTNE_ERR_WORKSPACE = 7      /* workspace missing, too small or misaligned   */
+};
+
+/* Population storage.  Compute is FP64 for LTNE_F64 and FP32 otherwise.
+   Every form stores deviations from the rest equilibrium: f_i - w_i rho_0
+   and g_i - w~_i T_0 (rho_0 = 1, T_0 = T_ref); the 16-bit forms scale the
+   deviation by a power of two before rounding to nearest even. */
+enum { LTNE_F64 = 0, LTNE_F32 = 1, LTNE_F16DEV = 2, LTNE_BF16DEV = 3 };
+
+/* Boundary modes.  CAVITY is the problem of Sec. 4; the other two are test
+   boxes: PERIODIC wraps both directions, CHANNEL wraps x and puts no-slip,
+   adiabatic walls at y = 0 and y = ny-1. */
+enum { LTNE_BC_CAVITY = 0, LTNE_BC_PERIODIC = 1, LTNE_BC_CHANNEL = 2 };
+
+/* Permeability model: DARCY takes K = Da L^2 at every node; ERGUN takes
+   Eq. 7, K = phi^3 d^2 / (150 (1-phi)^2), with d = d_p, or (d_p <= 0)
+   with d fixed so that the mean of K / L^2 over the nodes equals Da. */
+enum { LTNE_K_DARCY = 0, LTNE_K_ERGUN = 1 };
+
+/* Problem statement.  The dimensionless groups follow Sec. 2 (L73-79 of
+   the paper: Ra, Pr, Da, J_e, gamma_sf, sigma, H_v); relaxation rates and
+   varpi default to the values of Sec. 4.  Lattice mapping (the paper
+   leaves the velocity scale open): L = ny - 1, u_c = Ma c_s = sqrt(g beta
+   dT L), nu_f = u_c L sqrt(Pr/Ra), alpha_f = nu_f/Pr, nu_e = J_e nu_f,
+   alpha_s = (gamma_sf/sigma) alpha_f, s_nu from Eq. 23, zeta_alpha and
+   eta_alpha from Eq. 49 with c_sT^2 = varpi/2, and h_v/(rho c)_f =
+   H alpha_f / L^2. */
+typedef struct ltne_params {
+  int32_t nx, ny;          /* nodes including the wall nodes (>= 4 each)     */
+  int32_t storage;         /* LTNE_F64 | LTNE_F32 | LTNE_F16DEV | LTNE_BF16DEV */
+  int32_t bc;              /* LTNE_BC_*                                      */
+  int32_t permeability;    /* LTNE_K_DARCY | LTNE_K_ERGUN                    */
+  int32_t porosity_field;  /* 1: a per-node porosity is given to set_fields  */
+  double Ra, Pr, Da;       /* Rayleigh, Prandtl, Darcy (mean Da for ERGUN)   */
+  double porosity;         /* uniform porosity when porosity_field == 0      */
+  double H;                /* H_v = h_v L^2 / k_f                            */
+  double gamma_sf, sigma;  /* k_s/k_f, (rho c_p)_s/(rho c_p)_f               */
+  double J_e;              /* nu_e / nu_f                                    */
+  double T_hot, T_cold;    /* wall temperatures at x = 0 and x = nx-1        */
+  double T_ref;            /* Boussinesq T_0 of Eq. 6, also the deviation
+                              reference of the thermal populations          */
+  double Ma;               /* u_c / c_s (default 0.1)                        */
+  double F_phi;            /* < 0: Ergun F_phi = 1.75/sqrt(150 phi^3) (Eq. 7)
+                              per node; >= 0: this constant                 */
+  double d_p;              /* Ergun particle diameter (lattice units); <= 0:
+                              derived from the mean Darcy number            */
+  double qf, qs;           /* Q_f''', Q_s''' of Eq. 45 in lattice units      */
+  double s_e, s_eps, s_q;  /* Eq. 17                                         */
+  double zeta_e, zeta_nu;  /* Eq. 39                                         */
+  double eta_e, eta_nu;    /* Eq. 40                                         */
+  double varpi;            /* thermal weight parameter (Sec. 3.2), (0, 1)    */
+  double ext_ax, ext_ay;   /* extra body acceleration added to G (tests)     */
+  double nu_override;      /* > 0: nu_f in lattice units (needed for Ra = 0) */
+} ltne_params;
+
+/* Observables of the current state, reduced on the device in FP64.
+   Nu: (1/dT) * trapezoid over y of q(y) = -(dT/dx) at the wall, with the
+   second-order one-sided difference and the wall column at the imposed
+   wall temperature (the paper plots but never defines Nu).  residual:
+   max over {u, T_f, T_s} of ||X - X_prev|| / ||X|| against the previous
+   ltne_observables() call (NaN on the first call).  energy:
+   sum[phi T_f + (1-phi) sigma T_s] - sum[phi Q_f + (1-phi) sigma Q_s]/2,
+   which equals sum[phi sum g_f + (1-phi) sigma sum g_s] because the
+   interphase sources cancel. */
+typedef struct ltne_obs {
+  double Nu_f_hot, Nu_s_hot, Nu_f_cold, Nu_s_cold;
+  double residual;
+  double mass;             /* sum of rho                                     */
+  double energy;
+  double max_u;            /* max |u|                                        */
+  double max_dT;           /* max |T_f - T_s|                                */
+  double mean_Tf, mean_Ts;
+  double Fo;               /* alpha_f t / L^2 (the paper's Fo, L77, read as
+                              a dimensionless time)                          */
+  int64_t step;            /* steps taken since set_fields                   */
+  int64_t nonfinite;       /* number of nodes with a non-finite field        */
+} ltne_obs;
+
+typedef struct ltne_handle ltne_handle;
+
+/* Fill *p with the defaults (Sec. 4 rates, varpi = 2/5, J_e = sigma =
+   gamma_sf = 1, Ma = 0.1, T_hot = 1, T_cold = 0, T_ref = 0.5, Ergun F_phi,
+   FP32 storage, cavity, Darcy permeability). */
+void ltne_default_params(ltne_params* p, int32_t nx, int32_t ny);
+
+/* Validate *p, derive the lattice constants and create a handle bound to
+   cuda_stream (a cudaStream_t; NULL = legacy default stream).  Errors:
+   INVALID_ARG for sizes < 4, porosity outside (0,1), non-positive Pr,
+   sigma, varpi outside (0,1) etc.; UNSTABLE_TAU if any relaxation rate is
+   outside (0, 2).  No device memory is touched. */
+int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out);
+
+/* Bytes of device workspace the handle needs (populations in two
+   buffers, porosity, macroscopic fields, reduction partials). */
+size_t ltne_workspace_bytes(const ltne_handle* h);
+
+/* Bind caller-owned device memory (>= ltne_workspace_bytes, 256-byte
+   aligned).  The caller keeps it alive until ltne_destroy(). */
+int ltne_bind_workspace(ltne_handle* h, void* device_ptr, size_t bytes);
+
+/* Initial state S_0: equilibria of the given fields (Eqs. 24, 50, 51) at
+   every node, walls included.  porosity must be non-NULL iff
+   porosity_field was set (values in (0,1)); rho, ux, uy, T_f, T_s may be
+   NULL (defaults rho = 1, u = 0, T = T_ref).  Resets the step counter. */
+int ltne_set_fields(ltne_handle* h, const double* porosity, const double* rho,
+                    const double* ux, const double* uy, const double* T_f,
+                    const double* T_s);
+
+/* Advance n >= 0 time steps (collision, streaming and walls per step),
+   asynchronously on the handle's stream, replaying a cached CUDA graph of
+   steps where it can. */
+int ltne_step(ltne_handle* h, int64_t n);
+
+/* Reduce the current fields to *out (synchronises the stream).  Returns
+   LTNE_ERR_NONFINITE (with *out filled) if any field is NaN or Inf. */
+int ltne_observables(ltne_handle* h, ltne_obs* out);
+
+/* Copy the macroscopic fields of the current state to host arrays of
+   nx*ny doubles (any pointer may be NULL).  Synchronises the stream. */
+int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double* T_f,
+                    double* T_s);
+
+/* Checkpoint: size of the state blob, and copies of it to / from host
+   memory.  A restored handle continues bit for bit as if it had never
+   stopped.  Synchronises the stream. */
+size_t ltne_state_bytes(const ltne_handle* h);
+int ltne_get_state(ltne_handle* h, void* host, size_t bytes);
+int ltne_set_state(ltne_handle* h, const void* host, size_t bytes);
+
+/* Number of step-kernel launches issued by this handle so far. */
+int64_t ltne_launch_count(const ltne_handle* h);
+
+/* Free the handle's host state and graphs (not the workspace). */
+void ltne_destroy(ltne_handle* h);
+
+/* Name of a status code. */
+const char* ltne_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LTNE_H */

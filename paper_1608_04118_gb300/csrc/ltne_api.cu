@@ -1,0 +1,568 @@
+// ltne_api.cu -- host side of the C ABI declared in include/ltne.h: the
+// mapping from the paper's dimensionless groups (Sec. 2, Sec. 4) to lattice
+// constants, validation, the device workspace layout, CUDA-graph replay of
+// time steps, observables, field access and checkpoints.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ltne.h"
+#include "ltne_internal.h"
+
+using namespace ltne;
+
+namespace {
+
+constexpr int kGraphSteps = 32;  // steps per captured graph (even: keeps A-B parity)
+constexpr uint64_t kStateMagic = 0x4C544E4553544154ull;  // "LTNESTAT"
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t storage_bytes(int storage) {
+  switch (storage) {
+    case LTNE_F64: return 8;
+    case LTNE_F32: return 4;
+    default: return 2;
+  }
+}
+
+}  // namespace
+
+struct ltne_handle {
+  ltne_params p;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  NodeParams<double> P{};
+  StepShape shape;
+  // derived lattice values
+  double L = 0, nu_f = 0, alpha_f = 0;
+  // layout
+  int64_t pitch = 0, plane = 0;
+  size_t es = 0, ec = 0;  // storage / compute element sizes
+  size_t off_pop[2] = {0, 0}, off_phi = 0, off_mac = 0, off_prev = 0, off_part = 0, off_out = 0;
+  size_t ws_bytes = 0;
+  char* ws = nullptr;
+  int red_blocks = 1;
+  // state
+  int cur = 0;
+  int64_t step = 0;
+  bool fields_set = false;
+  bool have_prev = false;
+  float enc_scale = 1.0f;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t launches = 0;
+};
+
+namespace {
+
+int fail_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LTNE_OK;
+  cudaGetLastError();  // clear a sticky launch error from this thread's state
+  return LTNE_ERR_CUDA;
+}
+
+bool in_open(double v, double lo, double hi) { return v > lo && v < hi && isfinite(v); }
+
+// Lattice constants from the problem statement.  Returns a status code.
+int derive(ltne_handle* h, const double* porosity) {
+  const ltne_params& p = h->p;
+  NodeParams<double>& P = h->P;
+  const double L = p.ny - 1.0;
+  const double cs2 = 1.0 / 3.0;            // c_s^2 (below Eq. 23)
+  const double csT2 = p.varpi / 2.0;       // c_sT^2 (below Eq. 49)
+  const double uc = p.Ma * sqrt(cs2);      // velocity scale u_c = Ma c_s
+  const double dT = p.T_hot - p.T_cold;
+  const double gbeta = (p.Ra > 0 && dT != 0) ? uc * uc / (dT * L) : 0.0;  // u_c^2 = g b dT L
+  double nu_f;
+  if (p.nu_override > 0) nu_f = p.nu_override;
+  else if (p.Ra > 0) nu_f = uc * L * sqrt(p.Pr / p.Ra);  // from Ra = g b dT L^3 / (nu a)
+  else return LTNE_ERR_INVALID_ARG;
+  const double alpha_f = nu_f / p.Pr;
+  const double nu_e = p.J_e * nu_f;
+  const double alpha_s = p.gamma_sf / p.sigma * alpha_f;
+  h->L = L;
+  h->nu_f = nu_f;
+  h->alpha_f = alpha_f;
+
+  P.rho0 = 1.0;
+  P.T0 = p.T_ref;
+  P.s_e = p.s_e;
+  P.s_eps = p.s_eps;
+  P.s_q = p.s_q;
+  P.s_nu = 1.0 / (nu_e / cs2 + 0.5);           // Eq. 23
+  P.zeta_a = 1.0 / (alpha_f / csT2 + 0.5);     // Eq. 49
+  P.zeta_e = p.zeta_e;
+  P.zeta_nu = p.zeta_nu;
+  P.eta_a = 1.0 / (alpha_s / csT2 + 0.5);      // Eq. 49
+  P.eta_e = p.eta_e;
+  P.eta_nu = p.eta_nu;
+  P.c3 = -4.0 + 5.0 * p.varpi;
+  P.wt0 = 1.0 - p.varpi;
+  P.wt1 = p.varpi / 4.0;
+  P.gbeta = gbeta;
+  P.ext_ax = p.ext_ax;
+  P.ext_ay = p.ext_ay;
+  P.phi_u = p.porosity;
+  P.hcoef = p.H * alpha_f / (L * L);           // h_v/(rho c)_f from H_v = h_v L^2/k_f
+  P.sigma = p.sigma;
+  P.qf = p.qf;
+  P.qs = p.qs;
+  P.dT_hot = p.T_hot - p.T_ref;
+  P.dT_cold = p.T_cold - p.T_ref;
+  P.kmode = p.permeability == LTNE_K_ERGUN ? 1 : 0;
+  P.fmode = p.F_phi < 0 ? 1 : 0;
+  P.Fconst = p.F_phi < 0 ? 0.0 : p.F_phi;
+  if (P.kmode == 0) {
+    const double K = p.Da * L * L;             // Da = K / L^2
+    P.nu_over_K = nu_f / K;
+    P.inv_sqrtK = 1.0 / sqrt(K);
+    P.erg_a = P.erg_b = P.erg_c = 0.0;
+  } else {
+    double d = p.d_p;
+    if (d <= 0) {
+      // mean over the nodes of phi^3 / (1-phi)^2, so that mean K/L^2 = Da
+      double acc = 0.0;
+      const int64_t n = (int64_t)p.nx * p.ny;
+      if (porosity) {
+        for (int64_t k = 0; k < n; ++k) {
+          const double ph = porosity[k];
+          acc += ph * ph * ph / ((1 - ph) * (1 - ph));
+        }
+        acc /= (double)n;
+      } else {
+        const double ph = p.porosity;
+        acc = ph * ph * ph / ((1 - ph) * (1 - ph));
+      }
+      d = L * sqrt(150.0 * p.Da / acc);
+    }
+    P.erg_a = 150.0 * nu_f / (d * d);
+    P.erg_b = 1.75 / d;
+    P.erg_c = P.Fconst * sqrt(150.0) / d;
+    P.nu_over_K = P.inv_sqrtK = 0.0;
+  }
+  const double rates[] = {P.s_e, P.s_eps, P.s_q, P.s_nu, P.zeta_a, P.zeta_e,
+                          P.zeta_nu, P.eta_a, P.eta_e, P.eta_nu};
+  for (double r : rates)
+    if (!in_open(r, 0.0, 2.0)) return LTNE_ERR_UNSTABLE_TAU;
+  return LTNE_OK;
+}
+
+int validate(const ltne_params& p) {
+  if (p.nx < 4 || p.ny < 4) return LTNE_ERR_INVALID_ARG;
+  if ((int64_t)p.nx * p.ny > (int64_t)1 << 31) return LTNE_ERR_INVALID_ARG;
+  if (p.storage < LTNE_F64 || p.storage > LTNE_BF16DEV) return LTNE_ERR_INVALID_ARG;
+  if (p.bc < LTNE_BC_CAVITY || p.bc > LTNE_BC_CHANNEL) return LTNE_ERR_INVALID_ARG;
+  if (p.permeability != LTNE_K_DARCY && p.permeability != LTNE_K_ERGUN) return LTNE_ERR_INVALID_ARG;
+  if (!in_open(p.porosity, 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
+  if (!in_open(p.varpi, 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
+  if (!(p.Pr > 0) || !(p.sigma > 0) || !(p.J_e > 0) || !(p.gamma_sf > 0)) return LTNE_ERR_INVALID_ARG;
+  if (!(p.Da > 0) || !(p.Ma > 0) || !(p.H >= 0) || !(p.Ra >= 0)) return LTNE_ERR_INVALID_ARG;
+  const double vals[] = {p.Ra, p.Pr, p.Da, p.H, p.gamma_sf, p.sigma, p.J_e, p.T_hot, p.T_cold,
+                         p.T_ref, p.Ma, p.F_phi, p.d_p, p.qf, p.qs, p.ext_ax, p.ext_ay,
+                         p.nu_override};
+  for (double v : vals)
+    if (!isfinite(v)) return LTNE_ERR_INVALID_ARG;
+  return LTNE_OK;
+}
+
+void layout(ltne_handle* h) {
+  const ltne_params& p = h->p;
+  h->es = storage_bytes(p.storage);
+  h->ec = p.storage == LTNE_F64 ? 8 : 4;
+  h->pitch = (int64_t)align_up((size_t)p.nx, 64);
+  h->plane = (int64_t)align_up((size_t)(h->pitch * p.ny), 128);
+  const size_t A = 256;
+  size_t off = 0;
+  for (int b = 0; b < 2; ++b) {
+    h->off_pop[b] = off;
+    off = align_up(off + 19 * (size_t)h->plane * h->es, A);
+  }
+  h->off_phi = off;
+  if (p.porosity_field) off = align_up(off + (size_t)h->plane * h->ec, A);
+  h->off_mac = off;
+  off = align_up(off + 5 * (size_t)h->plane * h->ec, A);
+  h->off_prev = off;
+  off = align_up(off + 4 * (size_t)h->plane * h->ec, A);
+  h->red_blocks = reduce_blocks((int64_t)p.nx * p.ny);
+  h->off_part = off;
+  off = align_up(off + (size_t)h->red_blocks * NACC * sizeof(double), A);
+  h->off_out = off;
+  off = align_up(off + NACC * sizeof(double), A);
+  h->ws_bytes = off;
+  h->enc_scale = p.storage == LTNE_F16DEV ? 1024.0f : 1.0f;
+}
+
+LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
+  LatticeArgs a;
+  a.src = h->ws + h->off_pop[src_buf];
+  a.dst = h->ws + h->off_pop[src_buf ^ 1];
+  a.phi = h->p.porosity_field ? h->ws + h->off_phi : nullptr;
+  a.mac = h->ws + h->off_mac;
+  a.nx = h->p.nx;
+  a.ny = h->p.ny;
+  a.bc = h->p.bc;
+  a.write_macros = write_macros;
+  a.pitch = h->pitch;
+  a.plane = h->plane;
+  a.enc_scale = h->enc_scale;
+  return a;
+}
+
+cudaError_t launch_step(ltne_handle* h, int src_buf, int write_macros, cudaStream_t st) {
+  const LatticeArgs a = lattice_args(h, src_buf, write_macros);
+  switch (h->p.storage) {
+    case LTNE_F64: return launch_step_f64(a, h->P, h->shape, st);
+    case LTNE_F32: return launch_step_f32(a, h->P, h->shape, st);
+    case LTNE_F16DEV: return launch_step_f16(a, h->P, h->shape, st);
+    default: return launch_step_bf16(a, h->P, h->shape, st);
+  }
+}
+
+void drop_graphs(ltne_handle* h) {
+  for (auto& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// Capture kGraphSteps plain steps starting from buffer `parity`.
+cudaError_t build_graph(ltne_handle* h, int parity) {
+  cudaError_t e;
+  if (!h->cap_stream) {
+    e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  int b = parity;
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
+    le = launch_step(h, b, 0, h->cap_stream);
+    b ^= 1;
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ltne_default_params(ltne_params* p, int32_t nx, int32_t ny) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->storage = LTNE_F32;
+  p->bc = LTNE_BC_CAVITY;
+  p->permeability = LTNE_K_DARCY;
+  p->porosity_field = 0;
+  p->Ra = 1e4;
+  p->Pr = 1.0;
+  p->Da = 1e-2;
+  p->porosity = 0.6;
+  p->H = 10.0;
+  p->gamma_sf = 1.0;
+  p->sigma = 1.0;
+  p->J_e = 1.0;
+  p->T_hot = 1.0;
+  p->T_cold = 0.0;
+  p->T_ref = 0.5;
+  p->Ma = 0.1;
+  p->F_phi = -1.0;
+  p->d_p = 0.0;
+  p->s_e = 1.1;   // Sec. 4
+  p->s_eps = 1.1;
+  p->s_q = 1.2;
+  p->zeta_e = 1.1;
+  p->zeta_nu = 1.1;
+  p->eta_e = 1.1;
+  p->eta_nu = 1.1;
+  p->varpi = 0.4;
+}
+
+int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
+  if (!p || !out) return LTNE_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = validate(*p);
+  if (rc != LTNE_OK) return rc;
+  ltne_handle* h = new ltne_handle();
+  h->p = *p;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  rc = derive(h, nullptr);
+  if (rc != LTNE_OK) {
+    delete h;
+    return rc;
+  }
+  layout(h);
+  *out = h;
+  return LTNE_OK;
+}
+
+size_t ltne_workspace_bytes(const ltne_handle* h) { return h ? h->ws_bytes : 0; }
+
+int ltne_bind_workspace(ltne_handle* h, void* device_ptr, size_t bytes) {
+  if (!h || !device_ptr) return LTNE_ERR_INVALID_ARG;
+  if (bytes < h->ws_bytes || (reinterpret_cast<uintptr_t>(device_ptr) & 255u) != 0)
+    return LTNE_ERR_WORKSPACE;
+  drop_graphs(h);
+  h->ws = static_cast<char*>(device_ptr);
+  h->fields_set = false;
+  return LTNE_OK;
+}
+
+int ltne_set_fields(ltne_handle* h, const double* porosity, const double* rho, const double* ux,
+                    const double* uy, const double* T_f, const double* T_s) {
+  if (!h) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws) return LTNE_ERR_STATE;
+  const ltne_params& p = h->p;
+  if ((porosity != nullptr) != (p.porosity_field != 0)) return LTNE_ERR_INVALID_ARG;
+  const int64_t n = (int64_t)p.nx * p.ny;
+  if (porosity)
+    for (int64_t k = 0; k < n; ++k)
+      if (!in_open(porosity[k], 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
+  int rc = derive(h, porosity);
+  if (rc != LTNE_OK) return rc;
+  drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
+
+  // Stage the fields (compute type) into the macro planes, then k_init.
+  const double defaults[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
+  const double* src[5] = {rho, ux, uy, T_f, T_s};
+  std::vector<double> bd;
+  std::vector<float> bf;
+  const bool dbl = h->ec == 8;
+  if (dbl) bd.resize((size_t)n); else bf.resize((size_t)n);
+  auto stage = [&](const double* s, double dflt, char* dst) -> cudaError_t {
+    for (int64_t k = 0; k < n; ++k) {
+      const double v = s ? s[k] : dflt;
+      if (!isfinite(v)) return cudaErrorInvalidValue;
+      if (dbl) bd[(size_t)k] = v; else bf[(size_t)k] = (float)v;
+    }
+    const void* hs = dbl ? (const void*)bd.data() : (const void*)bf.data();
+    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->ec, hs, (size_t)p.nx * h->ec,
+                                      (size_t)p.nx * h->ec, (size_t)p.ny,
+                                      cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(h->stream);  // the staging buffer is reused
+  };
+  for (int k = 0; k < 5; ++k) {
+    cudaError_t e = stage(src[k], defaults[k], h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
+    if (e == cudaErrorInvalidValue) return LTNE_ERR_INVALID_ARG;
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  if (porosity) {
+    cudaError_t e = stage(porosity, 0.0, h->ws + h->off_phi);
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  cudaError_t e = cudaMemsetAsync(h->ws + h->off_prev, 0, 4 * (size_t)h->plane * h->ec, h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  LatticeArgs a = lattice_args(h, 1, 1);  // dst = buffer 0
+  switch (p.storage) {
+    case LTNE_F64: e = launch_init_f64(a, h->P, h->stream); break;
+    case LTNE_F32: e = launch_init_f32(a, h->P, h->stream); break;
+    case LTNE_F16DEV: e = launch_init_f16(a, h->P, h->stream); break;
+    default: e = launch_init_bf16(a, h->P, h->stream); break;
+  }
+  if (e != cudaSuccess) return fail_cuda(e);
+  h->cur = 0;
+  h->step = 0;
+  h->fields_set = true;
+  h->have_prev = false;
+  return LTNE_OK;
+}
+
+int ltne_step(ltne_handle* h, int64_t n) {
+  if (!h || n < 0) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  if (n == 0) return LTNE_OK;
+  int64_t plain = n - 1;  // the last step also writes the macroscopic fields
+  cudaError_t e;
+  while (plain >= kGraphSteps) {
+    if (!h->graph[h->cur]) {
+      e = build_graph(h, h->cur);
+      if (e != cudaSuccess) return fail_cuda(e);
+    }
+    e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    plain -= kGraphSteps;
+    h->step += kGraphSteps;
+    h->launches += kGraphSteps;
+  }
+  for (; plain > 0; --plain) {
+    e = launch_step(h, h->cur, 0, h->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    h->cur ^= 1;
+    ++h->step;
+    ++h->launches;
+  }
+  e = launch_step(h, h->cur, 1, h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  h->cur ^= 1;
+  ++h->step;
+  ++h->launches;
+  return LTNE_OK;
+}
+
+int ltne_observables(ltne_handle* h, ltne_obs* out) {
+  if (!h || !out) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  const ltne_params& p = h->p;
+  ReduceArgs a;
+  a.mac = h->ws + h->off_mac;
+  a.phi = p.porosity_field ? h->ws + h->off_phi : nullptr;
+  a.prev = h->ws + h->off_prev;
+  a.partials = reinterpret_cast<double*>(h->ws + h->off_part);
+  a.out = reinterpret_cast<double*>(h->ws + h->off_out);
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.pitch = h->pitch;
+  a.plane = h->plane;
+  a.phi_u = p.porosity;
+  a.sigma = p.sigma;
+  a.qf = p.qf;
+  a.qs = p.qs;
+  a.update_prev = 1;
+  a.blocks = h->red_blocks;
+  a.is_double = h->ec == 8;
+  cudaError_t e = launch_reduce(a, h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  double acc[NACC];
+  e = cudaMemcpyAsync(acc, a.out, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+
+  const double L = h->L, dT = p.T_hot - p.T_cold, nn = (double)p.nx * p.ny;
+  const bool cav = p.bc == LTNE_BC_CAVITY;
+  const double nan = NAN;
+  out->Nu_f_hot = cav ? (1.5 * p.T_hot * L + acc[A_NUF_H]) / dT : 0.0;
+  out->Nu_s_hot = cav ? (1.5 * p.T_hot * L + acc[A_NUS_H]) / dT : 0.0;
+  out->Nu_f_cold = cav ? (-1.5 * p.T_cold * L + acc[A_NUF_C]) / dT : 0.0;
+  out->Nu_s_cold = cav ? (-1.5 * p.T_cold * L + acc[A_NUS_C]) / dT : 0.0;
+  auto rel = [](double d2, double x2) { return d2 == 0 ? 0.0 : sqrt(d2 / x2); };
+  if (h->have_prev) {
+    out->residual = fmax(rel(acc[A_DU2], acc[A_U2]),
+                         fmax(rel(acc[A_DTF2], acc[A_TF2]), rel(acc[A_DTS2], acc[A_TS2])));
+  } else {
+    out->residual = nan;
+  }
+  h->have_prev = true;
+  out->mass = acc[A_MASS];
+  out->energy = acc[A_ENERGY];
+  out->max_u = acc[A_MAXU];
+  out->max_dT = acc[A_MAXDT];
+  out->mean_Tf = acc[A_SUMTF] / nn;
+  out->mean_Ts = acc[A_SUMTS] / nn;
+  out->Fo = h->alpha_f * (double)h->step / (L * L);
+  out->step = h->step;
+  out->nonfinite = (int64_t)acc[A_BAD];
+  return out->nonfinite > 0 ? LTNE_ERR_NONFINITE : LTNE_OK;
+}
+
+int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double* T_f, double* T_s) {
+  if (!h) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  const ltne_params& p = h->p;
+  const int64_t n = (int64_t)p.nx * p.ny;
+  double* dst[5] = {rho, ux, uy, T_f, T_s};
+  std::vector<char> tmp((size_t)n * h->ec);
+  for (int k = 0; k < 5; ++k) {
+    if (!dst[k]) continue;
+    cudaError_t e = cudaMemcpy2DAsync(tmp.data(), (size_t)p.nx * h->ec,
+                                      h->ws + h->off_mac + (size_t)k * h->plane * h->ec,
+                                      (size_t)h->pitch * h->ec, (size_t)p.nx * h->ec,
+                                      (size_t)p.ny, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (h->ec == 8) {
+      memcpy(dst[k], tmp.data(), (size_t)n * 8);
+    } else {
+      const float* t = reinterpret_cast<const float*>(tmp.data());
+      for (int64_t i = 0; i < n; ++i) dst[k][i] = t[i];
+    }
+  }
+  return LTNE_OK;
+}
+
+// State blob: 64-byte header, then the current populations (19 planes) and
+// the macroscopic planes (5), in the device layout.
+size_t ltne_state_bytes(const ltne_handle* h) {
+  if (!h) return 0;
+  return 64 + 19 * (size_t)h->plane * h->es + 5 * (size_t)h->plane * h->ec;
+}
+
+int ltne_get_state(ltne_handle* h, void* host, size_t bytes) {
+  if (!h || !host || bytes < ltne_state_bytes(h)) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  uint64_t hdr[8] = {kStateMagic, (uint64_t)h->p.storage, (uint64_t)h->p.nx,
+                     (uint64_t)h->p.ny, (uint64_t)h->step, (uint64_t)h->plane, 0, 0};
+  memcpy(host, hdr, sizeof(hdr));
+  char* dst = static_cast<char*>(host) + 64;
+  const size_t pb = 19 * (size_t)h->plane * h->es, mb = 5 * (size_t)h->plane * h->ec;
+  cudaError_t e = cudaMemcpyAsync(dst, h->ws + h->off_pop[h->cur], pb, cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst + pb, h->ws + h->off_mac, mb, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return fail_cuda(e);
+}
+
+int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
+  if (!h || !host || bytes < ltne_state_bytes(h)) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws) return LTNE_ERR_STATE;
+  uint64_t hdr[8];
+  memcpy(hdr, host, sizeof(hdr));
+  if (hdr[0] != kStateMagic || hdr[1] != (uint64_t)h->p.storage || hdr[2] != (uint64_t)h->p.nx ||
+      hdr[3] != (uint64_t)h->p.ny || hdr[5] != (uint64_t)h->plane)
+    return LTNE_ERR_INVALID_ARG;
+  const char* src = static_cast<const char*>(host) + 64;
+  const size_t pb = 19 * (size_t)h->plane * h->es, mb = 5 * (size_t)h->plane * h->ec;
+  cudaError_t e = cudaMemcpyAsync(h->ws + h->off_pop[0], src, pb, cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + h->off_mac, src + pb, mb, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  h->cur = 0;
+  h->step = (int64_t)hdr[4];
+  h->fields_set = true;
+  h->have_prev = false;
+  return LTNE_OK;
+}
+
+int64_t ltne_launch_count(const ltne_handle* h) { return h ? h->launches : 0; }
+
+void ltne_destroy(ltne_handle* h) {
+  if (!h) return;
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+const char* ltne_error_string(int code) {
+  switch (code) {
+    case LTNE_OK: return "LTNE_OK";
+    case LTNE_ERR_INVALID_ARG: return "LTNE_ERR_INVALID_ARG: invalid argument or parameter";
+    case LTNE_ERR_UNSTABLE_TAU: return "LTNE_ERR_UNSTABLE_TAU: a relaxation rate is outside (0, 2)";
+    case LTNE_ERR_CUDA: return "LTNE_ERR_CUDA: a CUDA runtime call failed";
+    case LTNE_ERR_NONFINITE: return "LTNE_ERR_NONFINITE: non-finite values in the fields";
+    case LTNE_ERR_TIMEOUT: return "LTNE_ERR_TIMEOUT: a bounded device wait gave up";
+    case LTNE_ERR_STATE: return "LTNE_ERR_STATE: call out of order";
+    case LTNE_ERR_WORKSPACE: return "LTNE_ERR_WORKSPACE: workspace missing, too small or misaligned";
+    default: return "LTNE_ERR_UNKNOWN";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// ltne_internal.h -- host-side declarations shared by the library's
+// translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ltne_node.cuh"
+
+namespace ltne {
+
+// Geometry and buffers of one lattice as the kernels see it.  Populations
+// are structure-of-arrays planes, index q*plane + y*pitch + x, in the order
+// f_0..f_8, g_f0..g_f4, g_s0..g_s4.  Rows are padded to a multiple of 64
+// elements and planes to a multiple of 256 bytes.
+struct LatticeArgs {
+  const void* src;   // post-collision populations of the last step
+  void* dst;         // populations written by this step
+  const void* phi;   // per-node porosity plane (compute type) or nullptr
+  void* mac;         // 5 macro planes (rho, ux, uy, Tf, Ts; compute type)
+  int nx, ny;
+  int bc;            // LTNE_BC_*
+  int write_macros;  // 1: also store the macroscopic fields of S_n
+  int64_t pitch;     // elements per row
+  int64_t plane;     // elements per plane
+  float enc_scale;   // 16-bit storage scale (power of two)
+};
+
+// Launch configuration of the step kernel (chosen by the autotuner).
+struct StepShape {
+  int bx = 128;
+  int by = 2;
+};
+
+// Per-storage-type launchers (one translation unit each).
+#define LTNE_DECLARE_LAUNCHERS(tag)                                                            \
+  cudaError_t launch_step_##tag(const LatticeArgs& a, const NodeParams<double>& P,             \
+                                StepShape s, cudaStream_t st);                                 \
+  cudaError_t launch_init_##tag(const LatticeArgs& a, const NodeParams<double>& P,             \
+                                cudaStream_t st);
+LTNE_DECLARE_LAUNCHERS(f64)
+LTNE_DECLARE_LAUNCHERS(f32)
+LTNE_DECLARE_LAUNCHERS(f16)
+LTNE_DECLARE_LAUNCHERS(bf16)
+#undef LTNE_DECLARE_LAUNCHERS
+
+// Observables reduction (FP64): accumulator slots.
+enum {
+  A_NUF_H = 0, A_NUS_H, A_NUF_C, A_NUS_C, A_MASS, A_ENERGY, A_MAXU, A_MAXDT, A_SUMTF,
+  A_SUMTS, A_DU2, A_U2, A_DTF2, A_TF2, A_DTS2, A_TS2, A_BAD, NACC
+};
+
+struct ReduceArgs {
+  const void* mac;   // 5 macro planes
+  const void* phi;   // porosity plane or nullptr
+  void* prev;        // 4 planes: ux, uy, Tf, Ts of the previous call
+  double* partials;  // [blocks][NACC] scratch
+  double* out;       // [NACC]
+  int nx, ny;
+  int64_t pitch, plane;
+  double phi_u, sigma, qf, qs;
+  int update_prev;
+  int blocks;
+  int is_double;     // macro planes hold doubles (else floats)
+};
+
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
+int reduce_blocks(int64_t nodes);
+
+}  // namespace ltne

@@ -1,0 +1,232 @@
+// ltne_step_impl.cuh -- fused collide-and-stream kernel of the
+// three-distribution MRT-LB method (Liu & He, arXiv:1608.04118), templated
+// on the population storage type S, the compute type C and the boundary
+// mode.  Included once per storage type by step_<tag>.cu.
+//
+// Memory scheme: two population buffers (A-B) hold post-collision values.
+// One thread owns one node and, in a single pass,
+//   1. pulls the post-collision values of the previous step from x - e_i
+//      (streaming, Eqs. 11, 34, 35), giving the pre-collision state S_n;
+//      a wall node instead pulls around its interior neighbour and rebuilds
+//      its populations by non-equilibrium extrapolation;
+//   2. computes the macroscopic values (Eqs. 6, 18, 20-22, 43-46) and the
+//      force (Eq. 5);
+//   3. collides (Eqs. 10, 32, 33) and writes its 19 post-collision values.
+// Per node and step this moves 19 reads + 19 writes of the storage type
+// (+ one porosity read when the porosity varies per node); the macroscopic
+// fields are written only on the last step of an ltne_step() call.
+#pragma once
+
+#include "ltne_internal.h"
+
+namespace ltne {
+
+template <typename C>
+__host__ NodeParams<C> cast_params(const NodeParams<double>& d) {
+  NodeParams<C> p;
+  p.rho0 = C(d.rho0); p.T0 = C(d.T0);
+  p.s_e = C(d.s_e); p.s_eps = C(d.s_eps); p.s_q = C(d.s_q); p.s_nu = C(d.s_nu);
+  p.zeta_a = C(d.zeta_a); p.zeta_e = C(d.zeta_e); p.zeta_nu = C(d.zeta_nu);
+  p.eta_a = C(d.eta_a); p.eta_e = C(d.eta_e); p.eta_nu = C(d.eta_nu);
+  p.c3 = C(d.c3); p.wt0 = C(d.wt0); p.wt1 = C(d.wt1);
+  p.gbeta = C(d.gbeta); p.ext_ax = C(d.ext_ax); p.ext_ay = C(d.ext_ay);
+  p.phi_u = C(d.phi_u); p.hcoef = C(d.hcoef); p.sigma = C(d.sigma);
+  p.qf = C(d.qf); p.qs = C(d.qs); p.dT_hot = C(d.dT_hot); p.dT_cold = C(d.dT_cold);
+  p.nu_over_K = C(d.nu_over_K); p.inv_sqrtK = C(d.inv_sqrtK); p.Fconst = C(d.Fconst);
+  p.erg_a = C(d.erg_a); p.erg_b = C(d.erg_b); p.erg_c = C(d.erg_c);
+  p.kmode = d.kmode; p.fmode = d.fmode;
+  return p;
+}
+
+// Boundary modes (values of LTNE_BC_*).
+constexpr int BC_CAVITY = 0, BC_PERIODIC = 1, BC_CHANNEL = 2;
+
+template <typename S, typename C>
+struct Pops {
+  // Loads the 19 post-collision values streaming into node (x, y):
+  // value i of node (x, y) at the new step is value i of (x - ex_i, y - ey_i).
+  // xm/xp and ym/yp are the columns/rows x-1, x+1, y-1, y+1 after wrapping.
+  static __device__ __forceinline__ void pull(const S* __restrict__ src, int64_t pitch,
+                                              int64_t plane, int x, int xm, int xp, int y,
+                                              int ym, int yp, C inv_scale, C (&f)[9],
+                                              C (&gf)[5], C (&gs)[5]) {
+    const int64_t r0 = (int64_t)y * pitch, rm = (int64_t)ym * pitch, rp = (int64_t)yp * pitch;
+    // D2Q9 e_i (Eq. 8): 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1)
+    //                   5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
+    const int64_t src_off[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x,
+                                rm + xm, rm + xp, rp + xp, rp + xm};
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      f[i] = Codec<S, C>::dec(src[(int64_t)i * plane + src_off[i]], inv_scale);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      gf[i] = Codec<S, C>::dec(src[(int64_t)(9 + i) * plane + src_off[i]], inv_scale);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      gs[i] = Codec<S, C>::dec(src[(int64_t)(14 + i) * plane + src_off[i]], inv_scale);
+  }
+
+  static __device__ __forceinline__ void store(S* __restrict__ dst, int64_t plane, int64_t off,
+                                               C scale, const C (&f)[9], const C (&gf)[5],
+                                               const C (&gs)[5]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dst[(int64_t)i * plane + off] = Codec<S, C>::enc(f[i], scale);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      dst[(int64_t)(9 + i) * plane + off] = Codec<S, C>::enc(gf[i], scale);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      dst[(int64_t)(14 + i) * plane + off] = Codec<S, C>::enc(gs[i], scale);
+  }
+};
+
+template <typename C>
+__device__ __forceinline__ void store_macros(C* __restrict__ mac, int64_t plane, int64_t off,
+                                             const NodeParams<C>& P, const Macro<C>& m) {
+  mac[off] = m.rho;
+  mac[plane + off] = m.ux;
+  mac[2 * plane + off] = m.uy;
+  mac[3 * plane + off] = P.T0 + m.dTf;
+  mac[4 * plane + off] = P.T0 + m.dTs;
+}
+
+template <typename S, typename C, int BC>
+__global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst,
+                                              const C* __restrict__ phi_field,
+                                              C* __restrict__ mac, const NodeParams<C> P,
+                                              const int nx, const int ny, const int64_t pitch,
+                                              const int64_t plane, const C scale,
+                                              const C inv_scale, const int write_macros) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+
+  // Wall classification and the node whose neighbourhood is pulled.
+  int cx = x, cy = y;
+  int kind = -1;  // -1 interior, 0 hot wall, 1 cold wall, 2 adiabatic / no-slip row
+  if (BC == BC_CAVITY) {
+    if (x == 0 || x == nx - 1) {
+      kind = (x == 0) ? 0 : 1;
+      cx = (x == 0) ? 1 : nx - 2;
+      if (y == 0) cy = 1;
+      else if (y == ny - 1) cy = ny - 2;
+    } else if (y == 0 || y == ny - 1) {
+      kind = 2;
+      cy = (y == 0) ? 1 : ny - 2;
+    }
+  } else if (BC == BC_CHANNEL) {
+    if (y == 0 || y == ny - 1) {
+      kind = 2;
+      cy = (y == 0) ? 1 : ny - 2;
+    }
+  }
+  int xm = cx - 1, xp = cx + 1, ym = cy - 1, yp = cy + 1;
+  if (BC == BC_PERIODIC || BC == BC_CHANNEL) {
+    xm = (cx == 0) ? nx - 1 : xm;
+    xp = (cx == nx - 1) ? 0 : xp;
+  }
+  if (BC == BC_PERIODIC) {
+    ym = (cy == 0) ? ny - 1 : ym;
+    yp = (cy == ny - 1) ? 0 : yp;
+  }
+
+  C f[9], gf[5], gs[5];
+  Pops<S, C>::pull(src, pitch, plane, cx, xm, xp, cy, ym, yp, inv_scale, f, gf, gs);
+
+  const int64_t off = (int64_t)y * pitch + x;
+  if (BC != BC_PERIODIC && kind >= 0) {
+    const C phin = phi_field ? phi_field[(int64_t)cy * pitch + cx] : P.phi_u;
+    Macro<C> mn;
+    macros<C>(P, phin, f, gf, gs, mn);
+    C dTwf = mn.dTf, dTws = mn.dTs;  // adiabatic: the neighbour's temperature
+    if (kind == 0) dTwf = dTws = P.dT_hot;
+    if (kind == 1) dTwf = dTws = P.dT_cold;
+    nee<C>(P, mn, dTwf, dTws, f, gf, gs);
+  }
+  const C phi = phi_field ? phi_field[off] : P.phi_u;
+  Macro<C> m;
+  macros<C>(P, phi, f, gf, gs, m);
+  if (write_macros) store_macros<C>(mac, plane, off, P, m);
+  collide<C>(P, m, f, gf, gs);
+  Pops<S, C>::store(dst, plane, off, scale, f, gf, gs);
+}
+
+// S_0 from the fields held in the macro planes (rho, ux, uy, Tf, Ts), then
+// its macroscopic values (overwriting the planes) and its collision.
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) k_init(S* __restrict__ dst,
+                                              const C* __restrict__ phi_field,
+                                              C* __restrict__ mac, const NodeParams<C> P,
+                                              const int nx, const int ny, const int64_t pitch,
+                                              const int64_t plane, const C scale) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const int64_t off = (int64_t)y * pitch + x;
+  const C phi = phi_field ? phi_field[off] : P.phi_u;
+  C f[9], gf[5], gs[5];
+  equilibrium<C>(P, phi, mac[off], mac[plane + off], mac[2 * plane + off], mac[3 * plane + off],
+                 mac[4 * plane + off], f, gf, gs);
+  Macro<C> m;
+  macros<C>(P, phi, f, gf, gs, m);
+  store_macros<C>(mac, plane, off, P, m);
+  collide<C>(P, m, f, gf, gs);
+  Pops<S, C>::store(dst, plane, off, scale, f, gf, gs);
+}
+
+template <typename S, typename C>
+cudaError_t launch_step_t(const LatticeArgs& a, const NodeParams<double>& Pd, StepShape s,
+                          cudaStream_t st) {
+  const NodeParams<C> P = cast_params<C>(Pd);
+  dim3 block(s.bx, s.by);
+  dim3 grid((a.nx + s.bx - 1) / s.bx, (a.ny + s.by - 1) / s.by);
+  const C scale = C(a.enc_scale), inv_scale = C(1.0 / a.enc_scale);
+  const S* src = static_cast<const S*>(a.src);
+  S* dst = static_cast<S*>(a.dst);
+  const C* phi = static_cast<const C*>(a.phi);
+  C* mac = static_cast<C*>(a.mac);
+  switch (a.bc) {
+    case BC_CAVITY:
+      k_step<S, C, BC_CAVITY><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny, a.pitch,
+                                                      a.plane, scale, inv_scale, a.write_macros);
+      break;
+    case BC_PERIODIC:
+      k_step<S, C, BC_PERIODIC><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
+                                                        a.pitch, a.plane, scale, inv_scale,
+                                                        a.write_macros);
+      break;
+    case BC_CHANNEL:
+      k_step<S, C, BC_CHANNEL><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
+                                                       a.pitch, a.plane, scale, inv_scale,
+                                                       a.write_macros);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename S, typename C>
+cudaError_t launch_init_t(const LatticeArgs& a, const NodeParams<double>& Pd, cudaStream_t st) {
+  const NodeParams<C> P = cast_params<C>(Pd);
+  dim3 block(128, 2);
+  dim3 grid((a.nx + 127) / 128, (a.ny + 1) / 2);
+  k_init<S, C><<<grid, block, 0, st>>>(static_cast<S*>(a.dst), static_cast<const C*>(a.phi),
+                                       static_cast<C*>(a.mac), P, a.nx, a.ny, a.pitch, a.plane,
+                                       C(a.enc_scale));
+  return cudaGetLastError();
+}
+
+}  // namespace ltne
+
+#define LTNE_DEFINE_LAUNCHERS(tag, S, C)                                                        \
+  namespace ltne {                                                                             \
+  cudaError_t launch_step_##tag(const LatticeArgs& a, const NodeParams<double>& P,             \
+                                StepShape s, cudaStream_t st) {                                \
+    return launch_step_t<S, C>(a, P, s, st);                                                   \
+  }                                                                                            \
+  cudaError_t launch_init_##tag(const LatticeArgs& a, const NodeParams<double>& P,             \
+                                cudaStream_t st) {                                             \
+    return launch_init_t<S, C>(a, P, st);                                                      \
+  }                                                                                            \
+  }

@@ -1,0 +1,281 @@
+"""Python binding of the ``ltne_*`` C ABI (include/ltne.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of ``libltne.so``.  PyTorch provides the device workspace and the
+stream.  If the library has not been built this module raises on load; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libltne.so")
+
+LTNE_OK = 0
+LTNE_ERR_INVALID_ARG = 1
+LTNE_ERR_UNSTABLE_TAU = 2
+LTNE_ERR_CUDA = 3
+LTNE_ERR_NONFINITE = 4
+LTNE_ERR_TIMEOUT = 5
+LTNE_ERR_STATE = 6
+LTNE_ERR_WORKSPACE = 7
+
+LTNE_F64, LTNE_F32, LTNE_F16DEV, LTNE_BF16DEV = 0, 1, 2, 3
+LTNE_BC_CAVITY, LTNE_BC_PERIODIC, LTNE_BC_CHANNEL = 0, 1, 2
+LTNE_K_DARCY, LTNE_K_ERGUN = 0, 1
+
+STORAGE = {"f64": LTNE_F64, "f32": LTNE_F32, "f16": LTNE_F16DEV, "bf16": LTNE_BF16DEV}
+
+
+class LtneError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = _lib().ltne_error_string(code).decode() if _lib_obj else "code %d" % code
+        super().__init__("%s%s" % (what + ": " if what else "", msg))
+
+
+class ltne_params(C.Structure):
+    """Mirror of ``struct ltne_params`` (field order and types as in ltne.h)."""
+
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("storage", C.c_int32), ("bc", C.c_int32),
+        ("permeability", C.c_int32), ("porosity_field", C.c_int32),
+        ("Ra", C.c_double), ("Pr", C.c_double), ("Da", C.c_double), ("porosity", C.c_double),
+        ("H", C.c_double), ("gamma_sf", C.c_double), ("sigma", C.c_double), ("J_e", C.c_double),
+        ("T_hot", C.c_double), ("T_cold", C.c_double), ("T_ref", C.c_double), ("Ma", C.c_double),
+        ("F_phi", C.c_double), ("d_p", C.c_double), ("qf", C.c_double), ("qs", C.c_double),
+        ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double),
+        ("zeta_e", C.c_double), ("zeta_nu", C.c_double), ("eta_e", C.c_double),
+        ("eta_nu", C.c_double), ("varpi", C.c_double),
+        ("ext_ax", C.c_double), ("ext_ay", C.c_double), ("nu_override", C.c_double),
+    ]
+
+
+class ltne_obs(C.Structure):
+    _fields_ = [
+        ("Nu_f_hot", C.c_double), ("Nu_s_hot", C.c_double), ("Nu_f_cold", C.c_double),
+        ("Nu_s_cold", C.c_double), ("residual", C.c_double), ("mass", C.c_double),
+        ("energy", C.c_double), ("max_u", C.c_double), ("max_dT", C.c_double),
+        ("mean_Tf", C.c_double), ("mean_Ts", C.c_double), ("Fo", C.c_double),
+        ("step", C.c_int64), ("nonfinite", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib_obj = None
+_lock = threading.Lock()
+
+# Every symbol include/ltne.h declares, with (restype, argtypes).
+_vp, _dp = C.c_void_p, C.POINTER(C.c_double)
+SIGNATURES = {
+    "ltne_default_params": (None, [C.POINTER(ltne_params), C.c_int32, C.c_int32]),
+    "ltne_create": (C.c_int, [C.POINTER(ltne_params), _vp, C.POINTER(_vp)]),
+    "ltne_workspace_bytes": (C.c_size_t, [_vp]),
+    "ltne_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "ltne_set_fields": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _dp]),
+    "ltne_step": (C.c_int, [_vp, C.c_int64]),
+    "ltne_observables": (C.c_int, [_vp, C.POINTER(ltne_obs)]),
+    "ltne_get_fields": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp]),
+    "ltne_state_bytes": (C.c_size_t, [_vp]),
+    "ltne_get_state": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "ltne_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "ltne_launch_count": (C.c_int64, [_vp]),
+    "ltne_destroy": (None, [_vp]),
+    "ltne_error_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def _lib():
+    global _lib_obj
+    with _lock:
+        if _lib_obj is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    "libltne.so is not built (%s); run __graft_entry__.build() or "
+                    "python -m paper_1608_04118_gb300.build -- there is no CPU fallback" % LIB_PATH)
+            lib = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib_obj = lib
+        return _lib_obj
+
+
+def load():
+    """Load libltne.so (raises ImportError if it is missing)."""
+    return _lib()
+
+
+def _check(code, what):
+    if code != LTNE_OK:
+        raise LtneError(code, what)
+
+
+def _f64(a, n):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+# ---- thin wrappers with the C names ---------------------------------------
+
+def ltne_default_params(nx, ny, **overrides) -> ltne_params:
+    p = ltne_params()
+    _lib().ltne_default_params(C.byref(p), int(nx), int(ny))
+    names = {f for f, _ in ltne_params._fields_}
+    for k, v in overrides.items():
+        if k == "storage" and isinstance(v, str):
+            v = STORAGE[v]
+        if k not in names:
+            raise KeyError("unknown parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def ltne_create(params: ltne_params, stream=None):
+    h = _vp()
+    s = _vp(int(stream) if stream is not None else 0)
+    _check(_lib().ltne_create(C.byref(params), s, C.byref(h)), "ltne_create")
+    return h
+
+
+def ltne_workspace_bytes(h) -> int:
+    return int(_lib().ltne_workspace_bytes(h))
+
+
+def ltne_bind_workspace(h, device_ptr: int, nbytes: int):
+    _check(_lib().ltne_bind_workspace(h, _vp(int(device_ptr)), int(nbytes)), "ltne_bind_workspace")
+
+
+def ltne_set_fields(h, nn, porosity=None, rho=None, ux=None, uy=None, T_f=None, T_s=None):
+    arrs = [_f64(a, nn) for a in (porosity, rho, ux, uy, T_f, T_s)]
+    _check(_lib().ltne_set_fields(h, *[_ptr(a) for a in arrs]), "ltne_set_fields")
+
+
+def ltne_step(h, n: int):
+    _check(_lib().ltne_step(h, int(n)), "ltne_step")
+
+
+def ltne_observables(h, allow_nonfinite=False) -> dict:
+    o = ltne_obs()
+    rc = _lib().ltne_observables(h, C.byref(o))
+    if not (rc == LTNE_OK or (allow_nonfinite and rc == LTNE_ERR_NONFINITE)):
+        raise LtneError(rc, "ltne_observables")
+    return o.as_dict()
+
+
+def ltne_get_fields(h, nx, ny) -> dict:
+    out = {k: np.empty(nx * ny) for k in ("rho", "ux", "uy", "Tf", "Ts")}
+    _check(_lib().ltne_get_fields(h, *[_ptr(out[k]) for k in ("rho", "ux", "uy", "Tf", "Ts")]),
+           "ltne_get_fields")
+    return {k: v.reshape(ny, nx) for k, v in out.items()}
+
+
+def ltne_state_bytes(h) -> int:
+    return int(_lib().ltne_state_bytes(h))
+
+
+def ltne_get_state(h) -> bytes:
+    n = ltne_state_bytes(h)
+    buf = (C.c_char * n)()
+    _check(_lib().ltne_get_state(h, C.cast(buf, _vp), n), "ltne_get_state")
+    return bytes(buf)
+
+
+def ltne_set_state(h, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(_lib().ltne_set_state(h, C.cast(buf, _vp), len(blob)), "ltne_set_state")
+
+
+def ltne_launch_count(h) -> int:
+    return int(_lib().ltne_launch_count(h))
+
+
+def ltne_destroy(h):
+    if h:
+        _lib().ltne_destroy(h)
+
+
+def ltne_error_string(code: int) -> str:
+    return _lib().ltne_error_string(int(code)).decode()
+
+
+# ---- convenience object ----------------------------------------------------
+
+class Cavity:
+    """One lattice on the current CUDA device with a torch-owned workspace.
+
+    ``Cavity(nx, ny, storage="f32", Ra=1e6, ...)`` takes any ltne_params
+    field as a keyword.  All device work runs on the current torch stream
+    unless ``stream`` is given.
+    """
+
+    def __init__(self, nx, ny, stream=None, device=None, **params):
+        import torch
+
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = ltne_default_params(nx, ny, **params)
+        dev = torch.device(device) if device is not None else torch.device("cuda",
+                                                                          torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        self.h = ltne_create(self.params, stream.cuda_stream)
+        nbytes = ltne_workspace_bytes(self.h)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        ltne_bind_workspace(self.h, self.workspace.data_ptr(), nbytes)
+
+    @property
+    def nodes(self):
+        return self.nx * self.ny
+
+    def set_fields(self, porosity=None, rho=None, ux=None, uy=None, T_f=None, T_s=None):
+        ltne_set_fields(self.h, self.nodes, porosity, rho, ux, uy, T_f, T_s)
+        return self
+
+    def step(self, n):
+        ltne_step(self.h, n)
+        return self
+
+    def observables(self, allow_nonfinite=False):
+        return ltne_observables(self.h, allow_nonfinite)
+
+    def fields(self):
+        return ltne_get_fields(self.h, self.nx, self.ny)
+
+    def get_state(self):
+        return ltne_get_state(self.h)
+
+    def set_state(self, blob):
+        ltne_set_state(self.h, blob)
+        return self
+
+    @property
+    def launches(self):
+        return ltne_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ltne_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,126 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol
+include/ltne.h declares, the Python records match the C layout, and the
+host-side validation returns the documented status codes."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lt():
+    from paper_1608_04118_gb300 import build
+
+    build.build()
+    from paper_1608_04118_gb300 import ltne
+
+    ltne.load()
+    return ltne
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(ltne_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lt):
+    names = declared_functions()
+    assert "ltne_step" in names and "ltne_create" in names
+    lib = C.CDLL(lt.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", lt.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\b(ltne_\w+)\b", out))
+    assert names <= exported
+    # the binding wraps exactly the declared functions
+    assert set(lt.SIGNATURES) == names
+
+
+def _c_layout(struct, fields):
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "ltne.h"', "int main(void){",
+           'printf("%%zu\\n", sizeof(%s));' % struct]
+    for f in fields:
+        src.append('printf("%%zu\\n", offsetof(%s, %s));' % (struct, f))
+    src.append("return 0;}")
+    d = os.path.join(ROOT, "_build")
+    os.makedirs(d, exist_ok=True)
+    c = os.path.join(d, "layout_%s.c" % struct)
+    exe = os.path.join(d, "layout_%s" % struct)
+    open(c, "w").write("\n".join(src))
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    return vals[0], vals[1:]
+
+
+@pytest.mark.parametrize("name", ["ltne_params", "ltne_obs"])
+def test_struct_layout_matches_header(lt, name):
+    py = getattr(lt, name)
+    fields = [f for f, _ in py._fields_]
+    size, offs = _c_layout(name, fields)
+    assert C.sizeof(py) == size
+    assert [getattr(py, f).offset for f in fields] == offs
+
+
+def test_defaults_follow_section4(lt):
+    p = lt.ltne_default_params(64, 64)
+    assert (p.s_e, p.s_eps, p.s_q) == (1.1, 1.1, 1.2)
+    assert (p.zeta_e, p.zeta_nu, p.eta_e, p.eta_nu) == (1.1, 1.1, 1.1, 1.1)
+    assert p.varpi == 0.4 and p.J_e == 1.0 and p.T_ref == 0.5
+
+
+def _create(lt, **kw):
+    p = lt.ltne_default_params(kw.pop("nx", 32), kw.pop("ny", 32), **kw)
+    h = C.c_void_p()
+    rc = lt.load().ltne_create(C.byref(p), None, C.byref(h))
+    if h:
+        lt.ltne_destroy(h)
+    return rc
+
+
+def test_create_validation_codes(lt):
+    assert _create(lt) == lt.LTNE_OK
+    assert _create(lt, nx=3) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, porosity=1.0) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, porosity=0.0) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, varpi=1.2) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, storage=9) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, Pr=float("nan")) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, Ra=0.0) == lt.LTNE_ERR_INVALID_ARG  # no viscosity without nu_override
+    assert _create(lt, Ra=0.0, nu_override=0.1) == lt.LTNE_OK
+    assert _create(lt, s_q=2.0) == lt.LTNE_ERR_UNSTABLE_TAU
+    assert _create(lt, nu_override=1e-7, Ra=0.0) == lt.LTNE_OK  # s_nu -> 2 from below
+    assert _create(lt, Ra=1e12, nx=8, ny=8) == lt.LTNE_OK
+    # thermal diffusivity so large that eta_alpha leaves (0, 2) cannot happen
+    # (it only tends to 0); a negative rate input is rejected
+    assert _create(lt, zeta_e=-0.5) == lt.LTNE_ERR_UNSTABLE_TAU
+
+
+def test_workspace_size_and_state_calls_without_gpu(lt):
+    p = lt.ltne_default_params(100, 70)
+    h = lt.ltne_create(p)
+    try:
+        nb = lt.ltne_workspace_bytes(h)
+        # two 19-plane population buffers of padded 128 x 70 fp32 planes at least
+        assert nb >= 2 * 19 * 128 * 70 * 4
+        lib = lt.load()
+        # calls that need a workspace report the order error, not a crash
+        assert lib.ltne_step(h, 1) == lt.LTNE_ERR_STATE
+        assert lib.ltne_set_fields(h, None, None, None, None, None, None) == lt.LTNE_ERR_STATE
+        assert lib.ltne_bind_workspace(h, C.c_void_p(256), 10) == lt.LTNE_ERR_WORKSPACE
+        assert lib.ltne_bind_workspace(h, C.c_void_p(257), nb) == lt.LTNE_ERR_WORKSPACE
+        assert lib.ltne_step(h, -1) == lt.LTNE_ERR_INVALID_ARG
+    finally:
+        lt.ltne_destroy(h)
+    assert lt.ltne_error_string(lt.LTNE_ERR_UNSTABLE_TAU).startswith("LTNE_ERR_UNSTABLE_TAU")

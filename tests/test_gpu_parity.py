@@ -1,0 +1,164 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 storage agrees with the oracle to rounding (rel-L2 of u,
+T_f, T_s <= 1e-10 after 10^4 steps); FP32 storage within rel-L2 <= 1e-5
+and Nusselt numbers within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_1608_04118_gb300 import workloads as W
+from tests.helpers import cavity_for, field_errors, oracle_for, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_04118_gb300 import build
+
+    build.build()
+    import oracle
+
+    oracle.build()
+
+
+TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+def _init_kw_oracle(fields):
+    if fields is None:
+        return {}
+    return dict(rho=fields["rho"], ux=fields["ux"], uy=fields["uy"], Tf=fields["T_f"],
+                Ts=fields["T_s"])
+
+
+def run_pair(cfg, steps, storage, phi=None, bc=0, fields=None):
+    o = oracle_for(cfg, phi=phi, bc=bc).init(**_init_kw_oracle(fields)).step(steps)
+    c = cavity_for(cfg, storage=storage, phi=phi, bc=bc)
+    c.set_fields(porosity=phi, **(fields or {})).step(steps)
+    return c, o
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("shape,bc,seed", [((8, 8), 0, 1), ((16, 16), 0, 2), ((13, 11), 0, 3),
+                                           ((9, 17), 1, 4), ((12, 10), 2, 5), ((5, 4), 0, 6)])
+def test_brute_force_small(storage, shape, bc, seed):
+    nx, ny = shape
+    cfg = W.random_params(seed, nx, ny)
+    fields = W.random_fields(nx, ny, seed + 100)
+    c, o = run_pair(cfg, 200, storage, bc=bc, fields=fields)
+    err = field_errors(c.fields(), o.macros())
+    for k in ("u", "Tf", "Ts"):
+        assert err[k] <= TOL[storage] * (1 if storage == "f64" else 2), (k, err)
+    assert err["rho_abs"] <= (1e-12 if storage == "f64" else 1e-6), err
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_multitile_ragged_per_node_porosity(storage):
+    """300 x 70 spans several 128-wide tiles with a ragged tail; per-node
+    porosity with the Ergun medium (Eq. 7) and d from the mean Da."""
+    nx, ny = 300, 70
+    cfg = dict(W.C2_THROUGHPUT, nx=nx, ny=ny, Ra=1e5)
+    phi = W.porosity_field(nx, ny, 0.3, 0.9, seed=21)
+    c, o = run_pair(cfg, 200, storage, phi=phi.reshape(-1))
+    err = field_errors(c.fields(), o.macros())
+    for k in ("u", "Tf", "Ts"):
+        assert err[k] <= TOL[storage], (k, err)
+
+
+def test_c1_cavity_full_run():
+    """The 64 x 64 cavity (Ra 1e4, Da 1e-2, phi 0.6, H 10) for 10^4 steps."""
+    cfg = W.C1_PLAIN_64
+    o = oracle_for(cfg).init().step(cfg["steps"])
+    ref, ob_ref = o.macros(), o.observables()
+    for storage in ("f64", "f32"):
+        c = cavity_for(cfg, storage=storage).set_fields().step(cfg["steps"])
+        err = field_errors(c.fields(), ref)
+        for k in ("u", "Tf", "Ts"):
+            assert err[k] <= TOL[storage], (storage, k, err)
+        ob = c.observables()
+        for k in ("Nu_f_hot", "Nu_s_hot", "Nu_f_cold", "Nu_s_cold"):
+            tol = 1e-10 if storage == "f64" else 1e-4
+            assert ob[k] == pytest.approx(ob_ref[k], rel=tol), (storage, k)
+        assert ob["mass"] == pytest.approx(ob_ref["mass"], rel=1e-12 if storage == "f64" else 1e-6)
+        assert ob["energy"] == pytest.approx(ob_ref["energy"],
+                                             rel=1e-12 if storage == "f64" else 1e-6)
+        assert ob["step"] == cfg["steps"]
+        assert ob["nonfinite"] == 0
+
+
+def test_observables_match_oracle_fp64():
+    cfg = dict(W.random_params(7, 33, 29))
+    phi = W.porosity_field(33, 29, 0.4, 0.8, seed=8).reshape(-1)
+    cfg["ergun"] = True
+    c, o = run_pair(cfg, 500, "f64", phi=phi)
+    ob, ref = c.observables(), o.observables()
+    for k in ("Nu_f_hot", "Nu_s_hot", "Nu_f_cold", "Nu_s_cold", "mass", "energy", "max_u",
+              "max_dT", "mean_Tf", "mean_Ts", "Fo"):
+        assert ob[k] == pytest.approx(ref[k], rel=1e-10, abs=1e-14), k
+    assert np.isnan(ob["residual"])
+    c.step(10)
+    ob2 = c.observables()
+    assert 0 < ob2["residual"] < 1
+
+
+def test_graph_replay_is_bitwise_equal_to_single_steps():
+    cfg = W.random_params(9, 70, 40)
+    a = cavity_for(cfg).set_fields()
+    b = cavity_for(cfg).set_fields()
+    a.step(100)  # graph replays + single launches
+    for _ in range(100):
+        b.step(1)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert a.get_state()[64:] == b.get_state()[64:]
+    assert a.launches == b.launches == 100
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+def test_checkpoint_resume_bitwise(storage):
+    cfg = W.random_params(10, 48, 40)
+    a = cavity_for(cfg, storage=storage).set_fields().step(150)
+    blob = a.get_state()
+    a.step(150)
+    b = cavity_for(cfg, storage=storage).set_state(blob).step(150)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), (storage, k)
+    assert b.observables()["step"] == 300
+
+
+def test_nonfinite_is_reported():
+    """A NaN planted in a checkpoint on the host surfaces as the non-finite
+    status of the observables (no device fault involved)."""
+    cfg = W.random_params(11, 32, 32)
+    a = cavity_for(cfg).set_fields().step(5)
+    blob = bytearray(a.get_state())
+    # first f_0 value of node (5, 5): header 64 bytes, plane 0, pitch 64 floats
+    off = 64 + 4 * (5 * 64 + 5)
+    blob[off:off + 4] = np.array([np.nan], dtype=np.float32).tobytes()
+    a.set_state(bytes(blob)).step(3)
+    from paper_1608_04118_gb300.ltne import LtneError, LTNE_ERR_NONFINITE
+
+    with pytest.raises(LtneError) as ei:
+        a.observables()
+    assert ei.value.code == LTNE_ERR_NONFINITE
+    assert a.observables(allow_nonfinite=True)["nonfinite"] > 0
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 5e-3), ("bf16", 3e-2)])
+def test_reduced_storage_error_bounded(storage, tol):
+    """FP16 / BF16 deviation storage with FP32 arithmetic on the 64 x 64
+    cavity after 2000 steps: errors against the FP64 oracle stay bounded."""
+    cfg = W.C1_PLAIN_64
+    o = oracle_for(cfg).init().step(2000)
+    c = cavity_for(cfg, storage=storage).set_fields().step(2000)
+    err = field_errors(c.fields(), o.macros())
+    for k in ("u", "Tf", "Ts"):
+        assert err[k] <= tol, (storage, k, err)
