@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+                    help="c2: single cavity (default, the headline line); c3: 256-cavity "
+                         "batch; c5: reduced-storage forms at 8192^2 with their errors")
     return ap.parse_args()
 
 
@@ -211,10 +214,158 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """256 independent cavities (sides 64..512, aspect 1-2, log-uniform Ra,
+    Da, H, conductivity ratio; seed 3) advanced by the batched kernel with
+    the autotuned schedule, against the same cavities run one by one through
+    ltne_step()."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1608_04118_gb300 import build as B
+
+    B.build()
+    from paper_1608_04118_gb300.autotune import tune_batch
+    from paper_1608_04118_gb300.ltne import Batch, Cavity
+
+    cavs = W.batch_cavities(256, seed=3)
+    stream = torch.cuda.Stream()
+    b = Batch(cavs, stream=stream)
+    t0 = time.perf_counter()
+    sched, t_best, table = tune_batch(b, steps=4, warmup=2)
+    tune_s = time.perf_counter() - t0
+    b.set_fields()
+    with torch.cuda.stream(stream):
+        b.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.launches
+    ev0.record(stream)
+    b.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    nodes = b.nodes
+    value = nodes * args.steps / t / 1e6
+    obs = b.observables()
+    # one by one: each cavity through the single-lattice path (its own
+    # graph-replayed ltne_step), a shorter run -- MLUPS is a rate
+    k_seq = min(args.steps, 200)
+    singles = []
+    for c in cavs:
+        cc = Cavity(c["nx"], c["ny"], stream=stream, storage="f32",
+                    **{k: v for k, v in c.items() if k not in ("nx", "ny")})
+        cc.set_fields()
+        singles.append(cc)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for cc in singles:
+        cc.step(k_seq)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = ev0.elapsed_time(ev1) / 1e3
+    seq = nodes * k_seq / t_seq / 1e6
+    peak, kind = load_peaks()
+    per_launch = t / args.steps
+    achieved = 152 * nodes / per_launch / 1e9
+    line = {"metric": "MLUPS (batched, 256 cavities)", "value": value, "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_launch * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256 porous LTNE cavities, sides 64..512, aspect 1-2, "
+                                   "seed 3", "nodes": nodes,
+                       "schedule": {"tile_x": sched[0], "tile_y": sched[1],
+                                    "blocks": sched[2], "tuning_s": tune_s,
+                                    "trials": len(table)}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": kind, "bytes_per_lup": 152},
+            "one_by_one": {"value": seq, "unit": UNIT, "steps": k_seq,
+                           "note": "same cavities, ltne_step() per cavity in sequence"},
+            "speedup_vs_one_by_one": value / seq,
+            "gpu_launches": int(b.launches - l0),
+            "nonfinite": int(sum(o["nonfinite"] for o in obs))}
+    print(json.dumps(line), flush=True)
+
+
+def run_reduced(args):
+    """MLUPS of FP16 / BF16 / FP32 storage at 8192^2 (physics of the
+    reduced-storage configuration) and their per-field errors against the
+    FP64 oracle on the down-sized 512^2 run."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1608_04118_gb300 import build as B
+
+    B.build()
+    from paper_1608_04118_gb300.ltne import Cavity
+    import oracle
+    from oracle import Oracle, OracleParams
+
+    c = W.C5_REDUCED
+    phys = {k: c[k] for k in ("Ra", "Pr", "Da", "porosity", "H", "gamma_sf", "sigma", "T_hot",
+                              "T_cold", "T_ref")}
+    n = args.n if args.n != 4096 else c["nx"]
+    stream = torch.cuda.Stream()
+    rates = {}
+    for st in ("f32", "f16", "bf16"):
+        cav = Cavity(n, n, stream=stream, storage=st, **phys).set_fields()
+        with torch.cuda.stream(stream):
+            cav.step(max(args.warmup, 3))
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        cav.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        rates[st] = n * n * args.steps / t / 1e6
+        cav.close()
+        del cav
+        torch.cuda.empty_cache()
+    m = c["parity_n"]
+    o = Oracle(OracleParams.make(m, m, **phys)).init().step(c["steps"])
+    ref, robs = o.macros(), o.observables()
+    errors = {}
+    for st in ("f32", "f16", "bf16"):
+        cav = Cavity(m, m, stream=stream, storage=st, **phys).set_fields().step(c["steps"])
+        got, gobs = cav.fields(), cav.observables()
+        e = {}
+        un = np.linalg.norm(np.stack([ref["ux"], ref["uy"]]))
+        e["u"] = float(np.linalg.norm(np.stack([got["ux"] - ref["ux"], got["uy"] - ref["uy"]])) / un)
+        for k in ("Tf", "Ts"):
+            e[k] = float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+        e["rho_minus_1"] = float(np.linalg.norm(got["rho"] - ref["rho"])
+                                 / np.linalg.norm(ref["rho"] - 1.0))
+        for k in ("Nu_f_hot", "Nu_s_hot", "Nu_f_cold", "Nu_s_cold"):
+            e[k] = float(abs(gobs[k] - robs[k]) / abs(robs[k]))
+        errors[st] = e
+    peak, kind = load_peaks()
+    bpl = {"f32": 152, "f16": 76, "bf16": 76}
+    line = {"metric": "MLUPS (reduced-storage forms)", "value": rates["f16"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 math, f16 storage",
+            "data": "synthetic",
+            "config": {"workload": "porous LTNE cavity %dx%d, phi 0.6, Da 1e-2, Ra 1e6, H 1000"
+                                   % (n, n), "parity_run": "%dx%d, %d steps vs FP64 oracle"
+                                                           % (m, m, c["steps"])},
+            "mlups": rates,
+            "roofline": {st: {"achieved": bpl[st] * rates[st] * 1e6 / 1e9, "peak": peak,
+                              "frac": bpl[st] * rates[st] * 1e6 / 1e9 / peak, "unit": "GB/s",
+                              "peak_kind": kind} for st in rates},
+            "errors_vs_fp64_oracle": errors, "oracle_cores": oracle.num_threads()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "c3":
+        run_batch(args)
+        return
+    if args.workload == "c5":
+        run_reduced(args)
         return
     import torch
 

@@ -188,6 +188,57 @@ void ltne_destroy(ltne_handle* h);
 /* Name of a status code. */
 const char* ltne_error_string(int code);
 
+/* ------------------------------------------------------------------------
+ * Batched form: `count` independent cavities of uneven size and parameters
+ * advanced together, one persistent launch per time step (replayed from a
+ * captured CUDA graph).  The per-node method is exactly that of
+ * ltne_step(); every cavity keeps its own walls (Sec. 4).  Restrictions:
+ * storage LTNE_F32, bc LTNE_BC_CAVITY, uniform porosity per cavity
+ * (porosity_field = 0).  Same ownership and stream rules as above.
+ * ---------------------------------------------------------------------- */
+typedef struct ltne_batch ltne_batch;
+
+/* Validate and derive every cavity's constants from params[0..count-1].
+   Errors as ltne_create, plus INVALID_ARG for a cavity outside the
+   restrictions above. */
+int ltne_batch_create(const ltne_params* params, int32_t count, void* cuda_stream,
+                      ltne_batch** out);
+
+/* Device workspace bytes (two population buffers for all cavities, macro
+   and snapshot planes, reduction scratch, the cavity table and the largest
+   tile list), and the total node count. */
+size_t ltne_batch_workspace_bytes(const ltne_batch* b);
+int64_t ltne_batch_nodes(const ltne_batch* b);
+
+/* Bind caller-owned device memory (>= workspace bytes, 256-byte aligned);
+   uploads the cavity table and the default schedule (128 x 2 tiles, one
+   block per tile). */
+int ltne_batch_bind_workspace(ltne_batch* b, void* device_ptr, size_t bytes);
+
+/* Launch schedule: tiles of tile_x x tile_y nodes (tile_x in 32..256 and
+   tile_y in 1..8, powers of two, 64 <= tile_x*tile_y <= 256; one thread per
+   node) walked by `blocks` persistent blocks (0: one block per tile). */
+int ltne_batch_set_schedule(ltne_batch* b, int32_t tile_x, int32_t tile_y, int32_t blocks);
+
+/* Every cavity at rest: rho = 1, u = 0, T_f = T_s = its T_ref (equilibrium
+   populations, walls included).  Resets the step counter. */
+int ltne_batch_set_fields(ltne_batch* b);
+
+/* Advance all cavities n >= 0 steps, asynchronously on the stream. */
+int ltne_batch_step(ltne_batch* b, int64_t n);
+
+/* Observables of every cavity into out[0..count-1] (synchronises). */
+int ltne_batch_observables(ltne_batch* b, ltne_obs* out);
+
+/* Fields of cavity `index` into host arrays of nx*ny doubles (synchronises). */
+int ltne_batch_get_fields(ltne_batch* b, int32_t index, double* rho, double* ux, double* uy,
+                          double* T_f, double* T_s);
+
+/* Number of step launches issued so far (one per time step). */
+int64_t ltne_batch_launch_count(const ltne_batch* b);
+
+void ltne_batch_destroy(ltne_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

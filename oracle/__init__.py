@@ -9,6 +9,7 @@ from .ltne_oracle import (  # noqa: F401
     Oracle,
     ComplexOracle,
     build,
+    ergun_diameter,
     lattice_tables,
     num_threads,
 )

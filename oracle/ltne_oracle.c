@@ -82,6 +82,8 @@ typedef struct orc_params {
   double T_hot, T_cold, T_ref, Ma, F_phi, d_p, qf, qs;
   double s_e, s_eps, s_q, zeta_e, zeta_nu, eta_e, eta_nu, varpi;
   double ext_ax, ext_ay, nu_override;
+  double L_ref;         /* > 0: characteristic length L (else ny - 1); lets a
+                           window of a larger cavity use that cavity's L  */
 } orc_params;
 
 /* Lattice data built once from the paper's definitions. */
@@ -184,7 +186,7 @@ static void build_lattice(orc_lattice* lat) {
 
 static void derive(orc_state* st, const double* phi_in) {
   const orc_params* p = &st->p;
-  st->L = (double)(p->ny - 1);
+  st->L = p->L_ref > 0 ? p->L_ref : (double)(p->ny - 1);
   st->cs2 = 1.0 / 3.0;                 /* c_s = c / sqrt(3), below Eq. 23 */
   st->csT2 = p->varpi / 2.0;           /* c_sT^2 = varpi c^2 / 2, Eq. 49   */
   double uc = p->Ma * sqrt(st->cs2);   /* reading R3 */
@@ -773,6 +775,15 @@ void orc_equilibria(const orc_state* st, double rho, double ux, double uy, doubl
   gseq(st, Ts, gse);
   meq_moments(rho, ux, uy, phi, me);
   forcing_S(st, rho, ux, uy, Fx, Fy, phi, S);
+}
+
+/* Ergun particle diameter that makes the mean of K / L^2 over the n given
+   porosities equal Da (Eq. 7 with the mean Darcy number). */
+double orc_ergun_diameter(const double* phi, long n, double L, double Da) {
+  double acc = 0.0;
+  for (long k = 0; k < n; ++k) acc += phi[k] * phi[k] * phi[k] / ((1 - phi[k]) * (1 - phi[k]));
+  acc /= n;
+  return L * sqrt(150.0 * Da / acc);
 }
 
 int orc_num_threads(void) {

@@ -56,6 +56,7 @@ class OracleParams(C.Structure):
         ("zeta_e", C.c_double), ("zeta_nu", C.c_double), ("eta_e", C.c_double),
         ("eta_nu", C.c_double), ("varpi", C.c_double),
         ("ext_ax", C.c_double), ("ext_ay", C.c_double), ("nu_override", C.c_double),
+        ("L_ref", C.c_double),
     ]
 
     # Defaults: relaxation rates and varpi from Sec. 4; T_0 midway between
@@ -65,7 +66,7 @@ class OracleParams(C.Structure):
         gamma_sf=1.0, sigma=1.0, J_e=1.0, T_hot=1.0, T_cold=0.0, T_ref=0.5, Ma=0.1,
         F_phi=-1.0, d_p=0.0, qf=0.0, qs=0.0, s_e=1.1, s_eps=1.1, s_q=1.2,
         zeta_e=1.1, zeta_nu=1.1, eta_e=1.1, eta_nu=1.1, varpi=0.4,
-        ext_ax=0.0, ext_ay=0.0, nu_override=0.0,
+        ext_ax=0.0, ext_ay=0.0, nu_override=0.0, L_ref=0.0,
     )
 
     @classmethod
@@ -110,6 +111,8 @@ def _load():
         lib.orc_node.argtypes = [C.c_void_p, C.c_int] + [dp] * 9
         lib.orc_equilibria.argtypes = [C.c_void_p] + [C.c_double] * 8 + [dp] * 5
         lib.orc_num_threads.restype = C.c_int
+        lib.orc_ergun_diameter.restype = C.c_double
+        lib.orc_ergun_diameter.argtypes = [dp, C.c_long, C.c_double, C.c_double]
         _lib = lib
         return lib
 
@@ -131,6 +134,12 @@ def _f64(a, n=None):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def ergun_diameter(phi, L, Da) -> float:
+    """Particle diameter giving mean(K)/L^2 = Da over the porosities phi."""
+    a = _f64(phi)
+    return float(_load().orc_ergun_diameter(_ptr(a), a.size, float(L), float(Da)))
 
 
 def lattice_tables():

@@ -1,0 +1,48 @@
+"""Launch-schedule autotuner for the batched form.
+
+Times candidate schedules (tile shape x persistent grid size) of a
+``Batch`` with CUDA events on its stream and keeps the fastest.  Candidate
+grid sizes are multiples of the SM count; 0 means one block per tile.
+"""
+from __future__ import annotations
+
+import itertools
+
+TILE_SHAPES = ((32, 4), (64, 2), (64, 4), (128, 1), (128, 2), (256, 1))
+BLOCKS_PER_SM = (2, 4, 8, 16)
+
+
+def candidates(sm_count):
+    for (tx, ty), k in itertools.product(TILE_SHAPES, BLOCKS_PER_SM + (0,)):
+        yield tx, ty, (k * sm_count if k else 0)
+
+
+def time_schedule(batch, schedule, steps, warmup=2):
+    import torch
+
+    batch.set_schedule(*schedule)
+    with torch.cuda.stream(batch.stream):
+        batch.step(warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(batch.stream)
+        batch.step(steps)
+        e1.record(batch.stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / steps
+
+
+def tune_batch(batch, steps=8, warmup=2):
+    """Pick the fastest schedule for ``batch`` (its state is advanced by the
+    trial steps; call ``set_fields`` afterwards).  Returns (schedule,
+    seconds per step, table of all trials)."""
+    import torch
+
+    sm = torch.cuda.get_device_properties(batch.workspace.device).multi_processor_count
+    batch.set_fields()
+    table = []
+    for sch in candidates(sm):
+        table.append((sch, time_schedule(batch, sch, steps, warmup)))
+    best = min(table, key=lambda r: r[1])
+    batch.set_schedule(*best[0])
+    return best[0], best[1], table

@@ -42,6 +42,7 @@ struct ltne_handle {
   int64_t pitch = 0, plane = 0;
   size_t es = 0, ec = 0;  // storage / compute element sizes
   size_t off_pop[2] = {0, 0}, off_phi = 0, off_mac = 0, off_prev = 0, off_part = 0, off_out = 0;
+  size_t off_tick = 0;
   size_t ws_bytes = 0;
   char* ws = nullptr;
   int red_blocks = 1;
@@ -65,10 +66,13 @@ int fail_cuda(cudaError_t e) {
 
 bool in_open(double v, double lo, double hi) { return v > lo && v < hi && isfinite(v); }
 
+}  // namespace
+
+namespace ltne {
+
 // Lattice constants from the problem statement.  Returns a status code.
-int derive(ltne_handle* h, const double* porosity) {
-  const ltne_params& p = h->p;
-  NodeParams<double>& P = h->P;
+int derive_params(const ltne_params& p, const double* porosity, NodeParams<double>& P,
+                  DerivedInfo& info) {
   const double L = p.ny - 1.0;
   const double cs2 = 1.0 / 3.0;            // c_s^2 (below Eq. 23)
   const double csT2 = p.varpi / 2.0;       // c_sT^2 (below Eq. 49)
@@ -82,9 +86,9 @@ int derive(ltne_handle* h, const double* porosity) {
   const double alpha_f = nu_f / p.Pr;
   const double nu_e = p.J_e * nu_f;
   const double alpha_s = p.gamma_sf / p.sigma * alpha_f;
-  h->L = L;
-  h->nu_f = nu_f;
-  h->alpha_f = alpha_f;
+  info.L = L;
+  info.nu_f = nu_f;
+  info.alpha_f = alpha_f;
 
   P.rho0 = 1.0;
   P.T0 = p.T_ref;
@@ -142,6 +146,27 @@ int derive(ltne_handle* h, const double* porosity) {
     P.erg_c = P.Fconst * sqrt(150.0) / d;
     P.nu_over_K = P.inv_sqrtK = 0.0;
   }
+  // Coefficients at the uniform porosity (used when no per-node field is
+  // set); the same definitions as the device's per-node evaluation.
+  {
+    Medium<double>& m = P.um;
+    const double ph = p.porosity;
+    m.phi = ph;
+    m.inv_phi = 1.0 / ph;
+    m.a = P.hcoef / ph;                                  // Eq. 42
+    m.b = P.hcoef / ((1.0 - ph) * p.sigma);
+    m.inv_1d = 1.0 / (1.0 + 0.5 * m.a + 0.5 * m.b);      // Eqs. 43-46
+    if (P.kmode == 0) {
+      m.c0 = P.nu_over_K;
+      m.c1 = (P.fmode == 0 ? P.Fconst : 1.75 / sqrt(150.0 * ph * ph * ph)) * P.inv_sqrtK;
+    } else {
+      const double om = 1.0 - ph, ip3 = 1.0 / (ph * ph * ph);
+      m.c0 = P.erg_a * om * om * ip3;
+      m.c1 = P.fmode == 1 ? P.erg_b * om * ip3 : P.erg_c * om / (ph * sqrt(ph));
+    }
+    m.l0 = 0.5 * (1.0 + 0.5 * ph * m.c0);                // Eq. 22
+    m.l1 = 0.5 * ph * m.c1;
+  }
   const double rates[] = {P.s_e, P.s_eps, P.s_q, P.s_nu, P.zeta_a, P.zeta_e,
                           P.zeta_nu, P.eta_a, P.eta_e, P.eta_nu};
   for (double r : rates)
@@ -149,7 +174,7 @@ int derive(ltne_handle* h, const double* porosity) {
   return LTNE_OK;
 }
 
-int validate(const ltne_params& p) {
+int validate_params(const ltne_params& p) {
   if (p.nx < 4 || p.ny < 4) return LTNE_ERR_INVALID_ARG;
   if ((int64_t)p.nx * p.ny > (int64_t)1 << 31) return LTNE_ERR_INVALID_ARG;
   if (p.storage < LTNE_F64 || p.storage > LTNE_BF16DEV) return LTNE_ERR_INVALID_ARG;
@@ -165,6 +190,56 @@ int validate(const ltne_params& p) {
   for (double v : vals)
     if (!isfinite(v)) return LTNE_ERR_INVALID_ARG;
   return LTNE_OK;
+}
+
+// Observables from the reduction accumulators of one lattice.
+int finish_observables(const ltne_params& p, const DerivedInfo& info, int64_t step,
+                       bool have_prev, const double* acc, ltne_obs* out) {
+  const double L = info.L, dT = p.T_hot - p.T_cold, nn = (double)p.nx * p.ny;
+  const bool cav = p.bc == LTNE_BC_CAVITY;
+  // The planes hold deviations from rho0 = 1 and T0 = T_ref; the reference
+  // parts of each sum are added here in FP64.  Over the trapezoid weights
+  // (sum L) the wall stencils carry -1.5 T0 L (hot) and +1.5 T0 L (cold).
+  const double T0 = p.T_ref;
+  out->Nu_f_hot = cav ? (1.5 * (p.T_hot - T0) * L + acc[A_NUF_H]) / dT : 0.0;
+  out->Nu_s_hot = cav ? (1.5 * (p.T_hot - T0) * L + acc[A_NUS_H]) / dT : 0.0;
+  out->Nu_f_cold = cav ? (-1.5 * (p.T_cold - T0) * L + acc[A_NUF_C]) / dT : 0.0;
+  out->Nu_s_cold = cav ? (-1.5 * (p.T_cold - T0) * L + acc[A_NUS_C]) / dT : 0.0;
+  auto rel = [](double d2, double x2) { return d2 == 0 ? 0.0 : sqrt(d2 / x2); };
+  // |T|^2 = sum (T0 + dT)^2
+  const double tf2 = nn * T0 * T0 + 2 * T0 * acc[A_SUMTF] + acc[A_TF2];
+  const double ts2 = nn * T0 * T0 + 2 * T0 * acc[A_SUMTS] + acc[A_TS2];
+  out->residual = have_prev ? fmax(rel(acc[A_DU2], acc[A_U2]),
+                                   fmax(rel(acc[A_DTF2], tf2), rel(acc[A_DTS2], ts2)))
+                            : NAN;
+  const double sphi = acc[A_SUMPHI];
+  out->mass = nn + acc[A_MASS];
+  // sum[phi T_f + (1-phi) sigma T_s] - sum[phi Q_f + (1-phi) sigma Q_s]/2
+  out->energy = acc[A_ENERGY] + T0 * (sphi + p.sigma * (nn - sphi))
+                - 0.5 * (p.qf * sphi + p.sigma * p.qs * (nn - sphi));
+  out->max_u = sqrt(acc[A_MAXU]);  // the pass accumulates max |u|^2
+  out->max_dT = acc[A_MAXDT];
+  out->mean_Tf = T0 + acc[A_SUMTF] / nn;
+  out->mean_Ts = T0 + acc[A_SUMTS] / nn;
+  out->Fo = info.alpha_f * (double)step / (L * L);
+  out->step = step;
+  out->nonfinite = (int64_t)acc[A_BAD];
+  return out->nonfinite > 0 ? LTNE_ERR_NONFINITE : LTNE_OK;
+}
+
+}  // namespace ltne
+
+namespace {
+
+int derive(ltne_handle* h, const double* porosity) {
+  DerivedInfo info;
+  const int rc = derive_params(h->p, porosity, h->P, info);
+  if (rc == LTNE_OK) {
+    h->L = info.L;
+    h->nu_f = info.nu_f;
+    h->alpha_f = info.alpha_f;
+  }
+  return rc;
 }
 
 void layout(ltne_handle* h) {
@@ -185,13 +260,15 @@ void layout(ltne_handle* h) {
   off = align_up(off + 5 * (size_t)h->plane * h->ec, A);
   h->off_prev = off;
   off = align_up(off + 4 * (size_t)h->plane * h->ec, A);
-  h->red_blocks = reduce_blocks((int64_t)p.nx * p.ny);
+  h->red_blocks = reduce_blocks(p.nx, p.ny);
   h->off_part = off;
   off = align_up(off + (size_t)h->red_blocks * NACC * sizeof(double), A);
   h->off_out = off;
   off = align_up(off + NACC * sizeof(double), A);
+  h->off_tick = off;  // two uint32 step counters for the stochastic rounding
+  off = align_up(off + 2 * sizeof(uint32_t), A);
   h->ws_bytes = off;
-  h->enc_scale = p.storage == LTNE_F16DEV ? 1024.0f : 1.0f;
+  h->enc_scale = p.storage == LTNE_F16DEV ? 1024.0f : 1.0f;  // FP16 deviations x 2^10
 }
 
 LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
@@ -207,6 +284,9 @@ LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
   a.pitch = h->pitch;
   a.plane = h->plane;
   a.enc_scale = h->enc_scale;
+  uint32_t* tick = reinterpret_cast<uint32_t*>(h->ws + h->off_tick);
+  a.tick_in = tick + src_buf;
+  a.tick_out = tick + (src_buf ^ 1);
   return a;
 }
 
@@ -295,7 +375,7 @@ void ltne_default_params(ltne_params* p, int32_t nx, int32_t ny) {
 int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
   if (!p || !out) return LTNE_ERR_INVALID_ARG;
   *out = nullptr;
-  int rc = validate(*p);
+  int rc = validate_params(*p);
   if (rc != LTNE_OK) return rc;
   ltne_handle* h = new ltne_handle();
   h->p = *p;
@@ -336,16 +416,18 @@ int ltne_set_fields(ltne_handle* h, const double* porosity, const double* rho, c
   if (rc != LTNE_OK) return rc;
   drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
 
-  // Stage the fields (compute type) into the macro planes, then k_init.
+  // Stage the fields as deviations (rho - 1, ux, uy, T - T_ref; compute
+  // type) into the macro planes, then k_init.
   const double defaults[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
+  const double refs[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
   const double* src[5] = {rho, ux, uy, T_f, T_s};
   std::vector<double> bd;
   std::vector<float> bf;
   const bool dbl = h->ec == 8;
   if (dbl) bd.resize((size_t)n); else bf.resize((size_t)n);
-  auto stage = [&](const double* s, double dflt, char* dst) -> cudaError_t {
+  auto stage = [&](const double* s, double dflt, double ref, char* dst) -> cudaError_t {
     for (int64_t k = 0; k < n; ++k) {
-      const double v = s ? s[k] : dflt;
+      const double v = (s ? s[k] : dflt) - ref;
       if (!isfinite(v)) return cudaErrorInvalidValue;
       if (dbl) bd[(size_t)k] = v; else bf[(size_t)k] = (float)v;
     }
@@ -357,15 +439,21 @@ int ltne_set_fields(ltne_handle* h, const double* porosity, const double* rho, c
     return cudaStreamSynchronize(h->stream);  // the staging buffer is reused
   };
   for (int k = 0; k < 5; ++k) {
-    cudaError_t e = stage(src[k], defaults[k], h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
+    cudaError_t e = stage(src[k], defaults[k], refs[k],
+                          h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
     if (e == cudaErrorInvalidValue) return LTNE_ERR_INVALID_ARG;
     if (e != cudaSuccess) return fail_cuda(e);
   }
   if (porosity) {
-    cudaError_t e = stage(porosity, 0.0, h->ws + h->off_phi);
+    cudaError_t e = stage(porosity, 0.0, 0.0, h->ws + h->off_phi);
     if (e != cudaSuccess) return fail_cuda(e);
   }
-  cudaError_t e = cudaMemsetAsync(h->ws + h->off_prev, 0, 4 * (size_t)h->plane * h->ec, h->stream);
+  // Zero both population buffers (row padding included, so that state
+  // blobs are deterministic) and the residual snapshot.
+  cudaError_t e = cudaMemsetAsync(h->ws + h->off_pop[0], 0, h->off_phi - h->off_pop[0], h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->ws + h->off_prev, 0, 4 * (size_t)h->plane * h->ec, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->off_tick, 0, 2 * sizeof(uint32_t), h->stream);
   if (e != cudaSuccess) return fail_cuda(e);
   LatticeArgs a = lattice_args(h, 1, 1);  // dst = buffer 0
   switch (p.storage) {
@@ -443,31 +531,13 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail_cuda(e);
 
-  const double L = h->L, dT = p.T_hot - p.T_cold, nn = (double)p.nx * p.ny;
-  const bool cav = p.bc == LTNE_BC_CAVITY;
-  const double nan = NAN;
-  out->Nu_f_hot = cav ? (1.5 * p.T_hot * L + acc[A_NUF_H]) / dT : 0.0;
-  out->Nu_s_hot = cav ? (1.5 * p.T_hot * L + acc[A_NUS_H]) / dT : 0.0;
-  out->Nu_f_cold = cav ? (-1.5 * p.T_cold * L + acc[A_NUF_C]) / dT : 0.0;
-  out->Nu_s_cold = cav ? (-1.5 * p.T_cold * L + acc[A_NUS_C]) / dT : 0.0;
-  auto rel = [](double d2, double x2) { return d2 == 0 ? 0.0 : sqrt(d2 / x2); };
-  if (h->have_prev) {
-    out->residual = fmax(rel(acc[A_DU2], acc[A_U2]),
-                         fmax(rel(acc[A_DTF2], acc[A_TF2]), rel(acc[A_DTS2], acc[A_TS2])));
-  } else {
-    out->residual = nan;
-  }
+  DerivedInfo info;
+  info.L = h->L;
+  info.nu_f = h->nu_f;
+  info.alpha_f = h->alpha_f;
+  const int rc = finish_observables(p, info, h->step, h->have_prev, acc, out);
   h->have_prev = true;
-  out->mass = acc[A_MASS];
-  out->energy = acc[A_ENERGY];
-  out->max_u = acc[A_MAXU];
-  out->max_dT = acc[A_MAXDT];
-  out->mean_Tf = acc[A_SUMTF] / nn;
-  out->mean_Ts = acc[A_SUMTS] / nn;
-  out->Fo = h->alpha_f * (double)h->step / (L * L);
-  out->step = h->step;
-  out->nonfinite = (int64_t)acc[A_BAD];
-  return out->nonfinite > 0 ? LTNE_ERR_NONFINITE : LTNE_OK;
+  return rc;
 }
 
 int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double* T_f, double* T_s) {
@@ -486,11 +556,13 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
     if (e != cudaSuccess) return fail_cuda(e);
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail_cuda(e);
+    const double ref = (k == 0) ? 1.0 : (k >= 3 ? p.T_ref : 0.0);  // planes hold deviations
     if (h->ec == 8) {
-      memcpy(dst[k], tmp.data(), (size_t)n * 8);
+      const double* t = reinterpret_cast<const double*>(tmp.data());
+      for (int64_t i = 0; i < n; ++i) dst[k][i] = ref + t[i];
     } else {
       const float* t = reinterpret_cast<const float*>(tmp.data());
-      for (int64_t i = 0; i < n; ++i) dst[k][i] = t[i];
+      for (int64_t i = 0; i < n; ++i) dst[k][i] = ref + (double)t[i];
     }
   }
   return LTNE_OK;
@@ -533,6 +605,9 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
                                   h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws + h->off_mac, src + pb, mb, cudaMemcpyHostToDevice, h->stream);
+  const uint32_t tick = (uint32_t)hdr[4];  // the rounding stream is keyed by the step
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + h->off_tick, &tick, sizeof(tick), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail_cuda(e);
   h->cur = 0;

@@ -1,0 +1,425 @@
+// ltne_batch.cu -- batched form: many independent cavities of uneven size
+// and parameters advanced by one persistent launch per time step, replayed
+// from a captured CUDA graph.  The per-node work is the same step_node() as
+// the single-lattice kernel (collision, streaming and walls of Liu & He's
+// three-distribution MRT-LB method, arXiv:1608.04118).
+//
+// Work decomposition: every cavity is cut into tiles of TX x TY nodes; the
+// tile list (cavity, x0, y0) is built on the host for the schedule the
+// autotuner picked.  A block of TX*TY threads walks the list with a stride of
+// the grid size (round-robin, so block loads differ by at most one tile),
+// stages the tile's cavity constants in shared memory and updates one node
+// per thread.  FP32 storage and arithmetic, uniform porosity per cavity.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ltne.h"
+#include "ltne_internal.h"
+#include "ltne_step_impl.cuh"
+
+using namespace ltne;
+
+namespace {
+
+constexpr int kGraphSteps = 32;
+
+struct BatchCavity {
+  int32_t nx, ny;
+  int64_t pitch, plane;
+  int64_t pop_off;  // element offset of the cavity's 19 planes in either buffer
+  int64_t mac_off;  // element offset of its 5 macro planes
+  int64_t prev_off; // element offset of its 4 residual snapshot planes
+  NodeParams<float> P;
+};
+
+constexpr int kParamWords = (int)(sizeof(NodeParams<float>) / sizeof(uint32_t));
+static_assert(sizeof(NodeParams<float>) % sizeof(uint32_t) == 0, "NodeParams<float> layout");
+static_assert(kParamWords <= 64, "cavity constants must fit one copy pass of >= 64 threads");
+
+__global__ void __launch_bounds__(256) k_batch_step(const float* __restrict__ src,
+                                                    float* __restrict__ dst,
+                                                    float* __restrict__ mac,
+                                                    const BatchCavity* __restrict__ cav,
+                                                    const int4* __restrict__ tiles, int ntiles,
+                                                    int tx_log2, int write_macros) {
+  __shared__ NodeParams<float> sP;
+  const int tid = threadIdx.x;
+  const int lx = tid & ((1 << tx_log2) - 1), ly = tid >> tx_log2;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 tl = tiles[t];  // (cavity, x0, y0, -)
+    __syncthreads();           // the previous tile is done with sP
+    if (tid < kParamWords)
+      reinterpret_cast<uint32_t*>(&sP)[tid] = reinterpret_cast<const uint32_t*>(&cav[tl.x].P)[tid];
+    __syncthreads();
+    const int nx = cav[tl.x].nx, ny = cav[tl.x].ny;
+    const int x = tl.y + lx, y = tl.z + ly;
+    if (x < nx && y < ny) {
+      const int64_t po = cav[tl.x].pop_off;
+      step_node<float, float, BC_CAVITY>(src + po, dst + po, nullptr, mac + cav[tl.x].mac_off, sP,
+                                         x, y, nx, ny, cav[tl.x].pitch, cav[tl.x].plane, 1.0f,
+                                         1.0f, write_macros, 0u);
+    }
+  }
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int fail_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LTNE_OK;
+  cudaGetLastError();
+  return LTNE_ERR_CUDA;
+}
+
+}  // namespace
+
+struct ltne_batch {
+  int count = 0;
+  std::vector<ltne_params> p;
+  std::vector<DerivedInfo> info;
+  std::vector<NodeParams<double>> Pd;
+  std::vector<BatchCavity> cav;
+  std::vector<bool> have_prev;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  // layout (bytes)
+  int64_t pop_elems = 0, mac_elems = 0, prev_elems = 0, max_tiles = 0;
+  int max_red_blocks = 1;
+  size_t off_pop[2] = {0, 0}, off_mac = 0, off_prev = 0, off_part = 0, off_out = 0, off_cav = 0,
+         off_tiles = 0, ws_bytes = 0;
+  char* ws = nullptr;
+  // schedule
+  int tx = 128, ty = 2, blocks = 0;
+  int64_t ntiles = 0;
+  bool schedule_uploaded = false;
+  // state
+  int cur = 0;
+  int64_t step = 0, launches = 0, nodes = 0;
+  bool fields_set = false;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+int64_t count_tiles(const ltne_batch* b, int tx, int ty) {
+  int64_t n = 0;
+  for (const auto& c : b->cav) n += (int64_t)((c.nx + tx - 1) / tx) * ((c.ny + ty - 1) / ty);
+  return n;
+}
+
+bool valid_shape(int tx, int ty) {
+  if (tx < 32 || tx > 256 || (tx & (tx - 1)) != 0) return false;
+  if (ty < 1 || ty > 8 || (ty & (ty - 1)) != 0) return false;
+  return tx * ty >= 64 && tx * ty <= 256;
+}
+
+void drop_graphs(ltne_batch* b) {
+  for (auto& g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int upload_schedule(ltne_batch* b) {
+  std::vector<int4> tl;
+  tl.reserve((size_t)count_tiles(b, b->tx, b->ty));
+  for (int c = 0; c < b->count; ++c)
+    for (int y0 = 0; y0 < b->cav[c].ny; y0 += b->ty)
+      for (int x0 = 0; x0 < b->cav[c].nx; x0 += b->tx) tl.push_back(make_int4(c, x0, y0, 0));
+  b->ntiles = (int64_t)tl.size();
+  if (b->ntiles > b->max_tiles) return LTNE_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(b->ws + b->off_tiles, tl.data(), tl.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  b->schedule_uploaded = true;
+  drop_graphs(b);
+  return LTNE_OK;
+}
+
+cudaError_t launch_batch_step(ltne_batch* b, int src_buf, int write_macros, cudaStream_t st) {
+  const int threads = b->tx * b->ty;
+  const int64_t grid64 = b->blocks > 0 ? (int64_t)b->blocks : b->ntiles;
+  const int grid = (int)(grid64 < 1 ? 1 : (grid64 > (1 << 30) ? (1 << 30) : grid64));
+  int tx_log2 = 0;
+  while ((1 << tx_log2) < b->tx) ++tx_log2;
+  k_batch_step<<<grid, threads, 0, st>>>(
+      reinterpret_cast<const float*>(b->ws + b->off_pop[src_buf]),
+      reinterpret_cast<float*>(b->ws + b->off_pop[src_buf ^ 1]),
+      reinterpret_cast<float*>(b->ws + b->off_mac),
+      reinterpret_cast<const BatchCavity*>(b->ws + b->off_cav),
+      reinterpret_cast<const int4*>(b->ws + b->off_tiles), (int)b->ntiles, tx_log2, write_macros);
+  return cudaGetLastError();
+}
+
+cudaError_t build_graph(ltne_batch* b, int parity) {
+  cudaError_t e;
+  if (!b->cap_stream) {
+    e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  int s = parity;
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
+    le = launch_batch_step(b, s, 0, b->cap_stream);
+    s ^= 1;
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->cap_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ltne_batch_create(const ltne_params* params, int32_t count, void* cuda_stream,
+                      ltne_batch** out) {
+  if (!params || !out || count < 1) return LTNE_ERR_INVALID_ARG;
+  *out = nullptr;
+  ltne_batch* b = new ltne_batch();
+  b->count = count;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->p.assign(params, params + count);
+  b->info.resize(count);
+  b->Pd.resize(count);
+  b->cav.resize(count);
+  b->have_prev.assign(count, false);
+  int64_t pop = 0, mac = 0, prev = 0;
+  for (int c = 0; c < count; ++c) {
+    const ltne_params& p = b->p[c];
+    int rc = validate_params(p);
+    if (rc == LTNE_OK && (p.storage != LTNE_F32 || p.bc != LTNE_BC_CAVITY || p.porosity_field))
+      rc = LTNE_ERR_INVALID_ARG;  // the batched form is FP32 cavities with uniform porosity
+    if (rc == LTNE_OK) rc = derive_params(p, nullptr, b->Pd[c], b->info[c]);
+    if (rc != LTNE_OK) {
+      delete b;
+      return rc;
+    }
+    BatchCavity& cv = b->cav[c];
+    cv.nx = p.nx;
+    cv.ny = p.ny;
+    cv.pitch = (int64_t)align_up((size_t)p.nx, 32);  // 128-byte rows
+    cv.plane = cv.pitch * p.ny;
+    cv.pop_off = pop;
+    cv.mac_off = mac;
+    cv.prev_off = prev;
+    cv.P = cast_params<float>(b->Pd[c]);
+    pop += 19 * cv.plane;
+    mac += 5 * cv.plane;
+    prev += 4 * cv.plane;
+    b->nodes += (int64_t)p.nx * p.ny;
+    const int rb = reduce_blocks(p.nx, p.ny);
+    if (rb > b->max_red_blocks) b->max_red_blocks = rb;
+  }
+  b->pop_elems = pop;
+  b->mac_elems = mac;
+  b->prev_elems = prev;
+  // capacity of the tile list: the largest count over every allowed shape
+  for (int tx = 32; tx <= 256; tx *= 2)
+    for (int ty = 1; ty <= 8; ty *= 2)
+      if (valid_shape(tx, ty)) {
+        const int64_t t = count_tiles(b, tx, ty);
+        if (t > b->max_tiles) b->max_tiles = t;
+      }
+  const size_t A = 256;
+  size_t off = 0;
+  for (int k = 0; k < 2; ++k) {
+    b->off_pop[k] = off;
+    off = align_up(off + (size_t)pop * sizeof(float), A);
+  }
+  b->off_mac = off;
+  off = align_up(off + (size_t)mac * sizeof(float), A);
+  b->off_prev = off;
+  off = align_up(off + (size_t)prev * sizeof(float), A);
+  b->off_part = off;
+  off = align_up(off + (size_t)b->max_red_blocks * NACC * sizeof(double), A);
+  b->off_out = off;
+  off = align_up(off + (size_t)count * NACC * sizeof(double), A);
+  b->off_cav = off;
+  off = align_up(off + (size_t)count * sizeof(BatchCavity), A);
+  b->off_tiles = off;
+  off = align_up(off + (size_t)b->max_tiles * sizeof(int4), A);
+  b->ws_bytes = off;
+  *out = b;
+  return LTNE_OK;
+}
+
+size_t ltne_batch_workspace_bytes(const ltne_batch* b) { return b ? b->ws_bytes : 0; }
+
+int64_t ltne_batch_nodes(const ltne_batch* b) { return b ? b->nodes : 0; }
+
+int ltne_batch_bind_workspace(ltne_batch* b, void* device_ptr, size_t bytes) {
+  if (!b || !device_ptr) return LTNE_ERR_INVALID_ARG;
+  if (bytes < b->ws_bytes || (reinterpret_cast<uintptr_t>(device_ptr) & 255u) != 0)
+    return LTNE_ERR_WORKSPACE;
+  drop_graphs(b);
+  b->ws = static_cast<char*>(device_ptr);
+  b->fields_set = false;
+  b->schedule_uploaded = false;
+  cudaError_t e = cudaMemcpyAsync(b->ws + b->off_cav, b->cav.data(),
+                                  b->cav.size() * sizeof(BatchCavity), cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  return upload_schedule(b);
+}
+
+int ltne_batch_set_schedule(ltne_batch* b, int32_t tile_x, int32_t tile_y, int32_t blocks) {
+  if (!b || !valid_shape(tile_x, tile_y) || blocks < 0) return LTNE_ERR_INVALID_ARG;
+  if (!b->ws) return LTNE_ERR_STATE;
+  b->tx = tile_x;
+  b->ty = tile_y;
+  b->blocks = blocks;
+  return upload_schedule(b);
+}
+
+int ltne_batch_set_fields(ltne_batch* b) {
+  if (!b) return LTNE_ERR_INVALID_ARG;
+  if (!b->ws || !b->schedule_uploaded) return LTNE_ERR_STATE;
+  // Rest state (rho = 1, u = 0, T = T_ref): all deviations zero.
+  cudaError_t e = cudaMemsetAsync(b->ws + b->off_pop[0], 0, b->off_part - b->off_pop[0], b->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  for (int c = 0; c < b->count && e == cudaSuccess; ++c) {
+    const BatchCavity& cv = b->cav[c];
+    LatticeArgs a{};
+    a.src = nullptr;
+    a.dst = b->ws + b->off_pop[0] + cv.pop_off * sizeof(float);
+    a.phi = nullptr;
+    a.mac = b->ws + b->off_mac + cv.mac_off * sizeof(float);
+    a.nx = cv.nx;
+    a.ny = cv.ny;
+    a.bc = LTNE_BC_CAVITY;
+    a.write_macros = 1;
+    a.pitch = cv.pitch;
+    a.plane = cv.plane;
+    a.enc_scale = 1.0f;
+    a.tick_in = nullptr;
+    a.tick_out = nullptr;
+    e = launch_init_f32(a, b->Pd[c], b->stream);
+  }
+  if (e != cudaSuccess) return fail_cuda(e);
+  b->cur = 0;
+  b->step = 0;
+  b->fields_set = true;
+  b->have_prev.assign(b->count, false);
+  return LTNE_OK;
+}
+
+int ltne_batch_step(ltne_batch* b, int64_t n) {
+  if (!b || n < 0) return LTNE_ERR_INVALID_ARG;
+  if (!b->ws || !b->fields_set) return LTNE_ERR_STATE;
+  if (n == 0) return LTNE_OK;
+  int64_t plain = n - 1;
+  cudaError_t e;
+  while (plain >= kGraphSteps) {
+    if (!b->graph[b->cur]) {
+      e = build_graph(b, b->cur);
+      if (e != cudaSuccess) return fail_cuda(e);
+    }
+    e = cudaGraphLaunch(b->graph[b->cur], b->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    plain -= kGraphSteps;
+    b->step += kGraphSteps;
+    b->launches += kGraphSteps;
+  }
+  for (; plain > 0; --plain) {
+    e = launch_batch_step(b, b->cur, 0, b->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    b->cur ^= 1;
+    ++b->step;
+    ++b->launches;
+  }
+  e = launch_batch_step(b, b->cur, 1, b->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  b->cur ^= 1;
+  ++b->step;
+  ++b->launches;
+  return LTNE_OK;
+}
+
+int ltne_batch_observables(ltne_batch* b, ltne_obs* out) {
+  if (!b || !out) return LTNE_ERR_INVALID_ARG;
+  if (!b->ws || !b->fields_set) return LTNE_ERR_STATE;
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < b->count && e == cudaSuccess; ++c) {
+    const BatchCavity& cv = b->cav[c];
+    ReduceArgs a;
+    a.mac = b->ws + b->off_mac + cv.mac_off * sizeof(float);
+    a.phi = nullptr;
+    a.prev = b->ws + b->off_prev + cv.prev_off * sizeof(float);
+    a.partials = reinterpret_cast<double*>(b->ws + b->off_part);  // reused in stream order
+    a.out = reinterpret_cast<double*>(b->ws + b->off_out) + (size_t)c * NACC;
+    a.nx = cv.nx;
+    a.ny = cv.ny;
+    a.pitch = cv.pitch;
+    a.plane = cv.plane;
+    a.phi_u = b->p[c].porosity;
+    a.sigma = b->p[c].sigma;
+    a.qf = b->p[c].qf;
+    a.qs = b->p[c].qs;
+    a.update_prev = 1;
+    a.blocks = reduce_blocks(cv.nx, cv.ny);
+    a.is_double = 0;
+    e = launch_reduce(a, b->stream);
+  }
+  if (e != cudaSuccess) return fail_cuda(e);
+  std::vector<double> acc((size_t)b->count * NACC);
+  e = cudaMemcpyAsync(acc.data(), b->ws + b->off_out, acc.size() * sizeof(double),
+                      cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  int rc = LTNE_OK;
+  for (int c = 0; c < b->count; ++c) {
+    const int r = finish_observables(b->p[c], b->info[c], b->step, b->have_prev[c],
+                                     acc.data() + (size_t)c * NACC, out + c);
+    b->have_prev[c] = true;
+    if (r != LTNE_OK) rc = r;
+  }
+  return rc;
+}
+
+int ltne_batch_get_fields(ltne_batch* b, int32_t index, double* rho, double* ux, double* uy,
+                          double* T_f, double* T_s) {
+  if (!b || index < 0 || index >= b->count) return LTNE_ERR_INVALID_ARG;
+  if (!b->ws || !b->fields_set) return LTNE_ERR_STATE;
+  const BatchCavity& cv = b->cav[index];
+  const int64_t n = (int64_t)cv.nx * cv.ny;
+  double* dst[5] = {rho, ux, uy, T_f, T_s};
+  const double T0 = b->p[index].T_ref;
+  std::vector<float> tmp((size_t)n);
+  for (int k = 0; k < 5; ++k) {
+    if (!dst[k]) continue;
+    const char* srcp = b->ws + b->off_mac + (cv.mac_off + (int64_t)k * cv.plane) * sizeof(float);
+    cudaError_t e = cudaMemcpy2DAsync(tmp.data(), (size_t)cv.nx * sizeof(float), srcp,
+                                      (size_t)cv.pitch * sizeof(float),
+                                      (size_t)cv.nx * sizeof(float), (size_t)cv.ny,
+                                      cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    const double ref = (k == 0) ? 1.0 : (k >= 3 ? T0 : 0.0);  // planes hold deviations
+    for (int64_t i = 0; i < n; ++i) dst[k][i] = ref + (double)tmp[(size_t)i];
+  }
+  return LTNE_OK;
+}
+
+int64_t ltne_batch_launch_count(const ltne_batch* b) { return b ? b->launches : 0; }
+
+void ltne_batch_destroy(ltne_batch* b) {
+  if (!b) return;
+  drop_graphs(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+}  // extern "C"

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ltne.h"
 #include "ltne_node.cuh"
 
 namespace ltne {
@@ -17,13 +18,15 @@ struct LatticeArgs {
   const void* src;   // post-collision populations of the last step
   void* dst;         // populations written by this step
   const void* phi;   // per-node porosity plane (compute type) or nullptr
-  void* mac;         // 5 macro planes (rho, ux, uy, Tf, Ts; compute type)
+  void* mac;         // 5 macro planes (rho-1, ux, uy, Tf-T0, Ts-T0; compute type)
   int nx, ny;
   int bc;            // LTNE_BC_*
   int write_macros;  // 1: also store the macroscopic fields of S_n
   int64_t pitch;     // elements per row
   int64_t plane;     // elements per plane
   float enc_scale;   // 16-bit storage scale (power of two)
+  const uint32_t* tick_in;  // step counter slot read by this step (16-bit forms)
+  uint32_t* tick_out;       // slot receiving the next step's counter
 };
 
 // Launch configuration of the step kernel (chosen by the autotuner).
@@ -47,11 +50,11 @@ LTNE_DECLARE_LAUNCHERS(bf16)
 // Observables reduction (FP64): accumulator slots.
 enum {
   A_NUF_H = 0, A_NUS_H, A_NUF_C, A_NUS_C, A_MASS, A_ENERGY, A_MAXU, A_MAXDT, A_SUMTF,
-  A_SUMTS, A_DU2, A_U2, A_DTF2, A_TF2, A_DTS2, A_TS2, A_BAD, NACC
+  A_SUMTS, A_DU2, A_U2, A_DTF2, A_TF2, A_DTS2, A_TS2, A_BAD, A_SUMPHI, NACC
 };
 
 struct ReduceArgs {
-  const void* mac;   // 5 macro planes
+  const void* mac;   // 5 macro planes (deviations: rho-1, ux, uy, Tf-T0, Ts-T0)
   const void* phi;   // porosity plane or nullptr
   void* prev;        // 4 planes: ux, uy, Tf, Ts of the previous call
   double* partials;  // [blocks][NACC] scratch
@@ -65,6 +68,17 @@ struct ReduceArgs {
 };
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
-int reduce_blocks(int64_t nodes);
+
+// Host-side parameter mapping and observables (ltne_api.cu), shared with
+// the batched form.
+struct DerivedInfo {
+  double L = 0, nu_f = 0, alpha_f = 0;
+};
+int validate_params(const ltne_params& p);
+int derive_params(const ltne_params& p, const double* porosity, NodeParams<double>& P,
+                  DerivedInfo& info);
+int finish_observables(const ltne_params& p, const DerivedInfo& info, int64_t step,
+                       bool have_prev, const double* acc, ltne_obs* out);
+int reduce_blocks(int nx, int ny);  // pass-1 blocks (= partial vectors)
 
 }  // namespace ltne

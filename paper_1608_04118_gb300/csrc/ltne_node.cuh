@@ -22,7 +22,21 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+// Per-node functions compile for host and device (the host copies serve
+// derivative checks of the reverse-mode functions).
+#define LTNE_HD __host__ __device__ __forceinline__
+
 namespace ltne {
+
+// Porosity-dependent coefficients of one node: exchange coefficients of
+// Eq. 42 (a = h_v/(phi (rho c)_f), b = h_v/((1-phi)(rho c)_s)), the factor
+// 1/(1 + d0 + d1) of Eqs. 43-44 (Eq. 46: d0 = a/2, d1 = b/2), the medium
+// coefficients c0 = nu_f/K and c1 = F_phi/sqrt(K) of Eqs. 5 and 7, and
+// l0, l1 of Eq. 22.
+template <typename C>
+struct Medium {
+  C phi, inv_phi, a, b, inv_1d, c0, c1, l0, l1;
+};
 
 // Lattice constants in compute type C, built from the paper's values.
 template <typename C>
@@ -49,41 +63,77 @@ struct NodeParams {
   C nu_over_K, inv_sqrtK, Fconst, erg_a, erg_b, erg_c;
   int kmode;                        // 0 Darcy, 1 Ergun
   int fmode;                        // 0 constant, 1 Ergun
+  Medium<C> um;                     // the coefficients at the uniform porosity
 };
 
 template <typename C>
 struct Macro {
   C rho, drho, ux, uy, umag;        // Eq. 18, Eq. 20
+  C jx, jy;                         // sum_i e_i f_i (deviations carry no momentum)
+  C sgf, sgs;                       // sum_i dg_i of both phases
   C dTf, dTs;                       // Eqs. 43-44 (minus T0)
+  C Srf, Srs;                       // Eq. 42 source strengths
   C Fx, Fy;                         // Eq. 5
   C a, b;                           // h_v/(phi (rho c)_f), h_v/((1-phi)(rho c)_s)
   C phi, inv_phi;
 };
 
-template <typename C> __device__ __forceinline__ C csqrt_(C x);
-template <> __device__ __forceinline__ float csqrt_<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double csqrt_<double>(double x) { return sqrt(x); }
+template <typename C> LTNE_HD C cfma_(C a, C b, C c);
+template <> LTNE_HD float cfma_<float>(float a, float b, float c) {
+  return fmaf(a, b, c);
+}
+template <> LTNE_HD double cfma_<double>(double a, double b, double c) {
+  return fma(a, b, c);
+}
 
-// c0 = nu_f/K and c1 = F_phi/sqrt(K) at porosity phi (Eqs. 5, 7, 22).
+// x / d for a small integer d, given rc = RN(1/d): one residual correction
+// (r = x - d q is exact in an FMA) removes the systematic bias that a plain
+// product with the rounded reciprocal would add at every step -- in FP32,
+// 6 RN(1/6) = 1 + 3e-8 would grow the momentum by that factor per step.
 template <typename C>
-__device__ __forceinline__ void medium(const NodeParams<C>& P, C phi, C inv_phi, C& c0, C& c1) {
+LTNE_HD C div_small(C x, C d, C rc) {
+  const C q = x * rc;
+  const C r = cfma_<C>(-d, q, x);
+  return cfma_<C>(r, rc, q);
+}
+
+template <typename C> LTNE_HD C csqrt_(C x);
+template <> LTNE_HD float csqrt_<float>(float x) { return sqrtf(x); }
+template <> LTNE_HD double csqrt_<double>(double x) { return sqrt(x); }
+
+// The coefficients at porosity phi (per-node porosity fields).
+//   Darcy K, constant F : c0 = nu_over_K, c1 = Fconst * inv_sqrtK
+//   Darcy K, Ergun F    : c1 = 1.75 / sqrt(150 phi^3) * inv_sqrtK
+//   Ergun K, Ergun F    : c0 = erg_a (1-phi)^2/phi^3, c1 = erg_b (1-phi)/phi^3
+//   Ergun K, constant F : c1 = erg_c (1-phi) / phi^(3/2)
+template <typename C>
+LTNE_HD Medium<C> medium_at(const NodeParams<C>& P, C phi) {
+  Medium<C> md;
+  md.phi = phi;
+  md.inv_phi = C(1) / phi;
+  md.a = P.hcoef * md.inv_phi;
+  md.b = P.hcoef / ((C(1) - phi) * P.sigma);
+  md.inv_1d = C(1) / (C(1) + C(0.5) * md.a + C(0.5) * md.b);
   if (P.kmode == 0) {
-    c0 = P.nu_over_K;
+    md.c0 = P.nu_over_K;
     if (P.fmode == 0) {
-      c1 = P.Fconst * P.inv_sqrtK;
+      md.c1 = P.Fconst * P.inv_sqrtK;
     } else {
-      c1 = C(1.75) / csqrt_<C>(C(150) * phi * phi * phi) * P.inv_sqrtK;
+      md.c1 = C(1.75) / csqrt_<C>(C(150) * phi * phi * phi) * P.inv_sqrtK;
     }
   } else {
-    C om = C(1) - phi;
-    C ip3 = inv_phi * inv_phi * inv_phi;
-    c0 = P.erg_a * om * om * ip3;
+    const C om = C(1) - phi;
+    const C ip3 = md.inv_phi * md.inv_phi * md.inv_phi;
+    md.c0 = P.erg_a * om * om * ip3;
     if (P.fmode == 1) {
-      c1 = P.erg_b * om * ip3;
+      md.c1 = P.erg_b * om * ip3;
     } else {
-      c1 = P.erg_c * om * inv_phi / csqrt_<C>(phi);
+      md.c1 = P.erg_c * om * md.inv_phi / csqrt_<C>(phi);
     }
   }
+  md.l0 = C(0.5) * (C(1) + C(0.5) * phi * md.c0);  // Eq. 22
+  md.l1 = C(0.5) * phi * md.c1;
+  return md;
 }
 
 // Macroscopic values of a node from its pre-collision deviations:
@@ -91,38 +141,41 @@ __device__ __forceinline__ void medium(const NodeParams<C>& P, C phi, C inv_phi,
 // gravity along -y), density (Eq. 18), velocity by the explicit root of the
 // implicit Eq. 19 (Eqs. 20-22) and the total force (Eq. 5).
 template <typename C>
-__device__ __forceinline__ void macros(const NodeParams<C>& P, C phi, const C (&f)[9],
-                                       const C (&gf)[5], const C (&gs)[5], Macro<C>& m) {
+LTNE_HD void macros(const NodeParams<C>& P, const Medium<C>& md,
+                                       const C (&f)[9], const C (&gf)[5], const C (&gs)[5],
+                                       Macro<C>& m) {
+  const C phi = md.phi;
   m.phi = phi;
-  m.inv_phi = C(1) / phi;
-  m.a = P.hcoef * m.inv_phi;
-  m.b = P.hcoef / ((C(1) - phi) * P.sigma);
-  const C d0 = C(0.5) * m.a, d1 = C(0.5) * m.b;
-  const C dAf = (gf[0] + gf[1] + gf[2] + gf[3] + gf[4]) + C(0.5) * P.qf;
-  const C dAs = (gs[0] + gs[1] + gs[2] + gs[3] + gs[4]) + C(0.5) * P.qs;
-  const C inv = C(1) / (C(1) + d0 + d1);
-  m.dTf = ((C(1) + d1) * dAf + d0 * dAs) * inv;
-  m.dTs = (d1 * dAf + (C(1) + d0) * dAs) * inv;
+  m.inv_phi = md.inv_phi;
+  m.a = md.a;
+  m.b = md.b;
+  m.sgf = (gf[0] + gf[1]) + (gf[2] + gf[3]) + gf[4];
+  m.sgs = (gs[0] + gs[1]) + (gs[2] + gs[3]) + gs[4];
+  // Eqs. 43-44 solve T = sum g + Sr/2 (Eqs. 41-42).  They are evaluated
+  // through the phase difference D = T_f - T_s = (A_f - A_s)/(1 + d0 + d1),
+  // A = sum g + Q/2, so that each temperature is its population sum plus a
+  // small exchange correction and no rounded factor multiplies the sum.
+  const C D = ((m.sgf - m.sgs) + C(0.5) * (P.qf - P.qs)) * md.inv_1d;
+  m.Srf = P.qf - m.a * D;
+  m.Srs = P.qs + m.b * D;
+  m.dTf = m.sgf + C(0.5) * m.Srf;
+  m.dTs = m.sgs + C(0.5) * m.Srs;
   const C Gx = P.ext_ax;
   const C Gy = P.gbeta * m.dTf + P.ext_ay;
 
   m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   m.rho = P.rho0 + m.drho;
-  const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-  const C jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  m.jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  m.jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
   const C inv_rho = C(1) / m.rho;
-  const C vx = jx * inv_rho + C(0.5) * phi * Gx;  // Eq. 21
-  const C vy = jy * inv_rho + C(0.5) * phi * Gy;
-  C c0, c1;
-  medium<C>(P, phi, m.inv_phi, c0, c1);
-  const C l0 = C(0.5) * (C(1) + C(0.5) * phi * c0);  // Eq. 22
-  const C l1 = C(0.5) * phi * c1;
+  const C vx = m.jx * inv_rho + C(0.5) * phi * Gx;  // Eq. 21
+  const C vy = m.jy * inv_rho + C(0.5) * phi * Gy;
   const C vmag = csqrt_<C>(vx * vx + vy * vy);
-  const C inv_den = C(1) / (l0 + csqrt_<C>(l0 * l0 + l1 * vmag));  // Eq. 20
+  const C inv_den = C(1) / (md.l0 + csqrt_<C>(md.l0 * md.l0 + md.l1 * vmag));  // Eq. 20
   m.ux = vx * inv_den;
   m.uy = vy * inv_den;
   m.umag = vmag * inv_den;
-  const C drag = c0 + c1 * m.umag;
+  const C drag = md.c0 + md.c1 * m.umag;
   m.Fx = phi * (Gx - drag * m.ux);  // Eq. 5
   m.Fy = phi * (Gy - drag * m.uy);
 }
@@ -137,7 +190,7 @@ __device__ __forceinline__ void macros(const NodeParams<C>& P, C phi, const C (&
 // Temperatures: n* = n - Q (n - n^eq) + (I - Q/2) Psi (Eqs. 32-33) with
 // n^eq of Eqs. 37-38 and Psi = Sr (1, 0, 0, -4 + 5 varpi, 0) (Eqs. 29-31).
 template <typename C>
-__device__ __forceinline__ void collide(const NodeParams<C>& P, const Macro<C>& m, C (&f)[9],
+LTNE_HD void collide(const NodeParams<C>& P, const Macro<C>& m, C (&f)[9],
                                         C (&gf)[5], C (&gs)[5]) {
   const C rho = m.rho, ux = m.ux, uy = m.uy, Fx = m.Fx, Fy = m.Fy, ip = m.inv_phi;
   // ---- flow: deviation moments M df
@@ -155,7 +208,7 @@ __device__ __forceinline__ void collide(const NodeParams<C>& P, const Macro<C>& 
   const C ru2 = C(3) * rho * (ux * ux + uy * uy) * ip;
   const C meq1 = C(-2) * m.drho + ru2;
   const C meq2 = m.drho - ru2;
-  const C rux = rho * ux, ruy = rho * uy;
+  const C rux = rho * ux, ruy = rho * uy;  // m^eq_3, m^eq_5 (Eq. 15)
   const C meq7 = rho * (ux * ux - uy * uy) * ip;
   const C meq8 = rho * ux * uy * ip;
   // forcing moments
@@ -167,16 +220,22 @@ __device__ __forceinline__ void collide(const NodeParams<C>& P, const Macro<C>& 
   const C ms0 = m.drho;
   const C ms1 = m1 - P.s_e * (m1 - meq1) + (C(1) - C(0.5) * P.s_e) * S1;
   const C ms2 = m2 - P.s_eps * (m2 - meq2) - (C(1) - C(0.5) * P.s_eps) * S1;
-  const C ms3 = rux + C(0.5) * rFx;  // s_3 = 1
+  // s_3 = s_5 = 1: m*_3 = rho ux + rho Fx / 2 = j_x + rho Fx by Eq. 19, so
+  // the momentum passes through exactly and only the force is added.
+  const C ms3 = m.jx + rFx;
   const C ms4 = m4 - P.s_q * (m4 + rux) - (C(1) - C(0.5) * P.s_q) * rFx;
-  const C ms5 = ruy + C(0.5) * rFy;  // s_5 = 1
+  const C ms5 = m.jy + rFy;
   const C ms6 = m6 - P.s_q * (m6 + ruy) - (C(1) - C(0.5) * P.s_q) * rFy;
   const C ms7 = m7 - P.s_nu * (m7 - meq7) + (C(1) - C(0.5) * P.s_nu) * S7;
   const C ms8 = m8 - P.s_nu * (m8 - meq8) + (C(1) - C(0.5) * P.s_nu) * S8;
   // df* = M^-1 m*
-  const C r0 = ms0 * C(1.0 / 9.0), r1 = ms1 * C(1.0 / 36.0), r2 = ms2 * C(1.0 / 36.0);
-  const C r3 = ms3 * C(1.0 / 6.0), r4 = ms4 * C(1.0 / 12.0);
-  const C r5 = ms5 * C(1.0 / 6.0), r6 = ms6 * C(1.0 / 12.0);
+  const C r0 = div_small<C>(ms0, C(9), C(1.0 / 9.0));
+  const C r1 = div_small<C>(ms1, C(36), C(1.0 / 36.0));
+  const C r2 = div_small<C>(ms2, C(36), C(1.0 / 36.0));
+  const C r3 = div_small<C>(ms3, C(6), C(1.0 / 6.0));
+  const C r4 = div_small<C>(ms4, C(12), C(1.0 / 12.0));
+  const C r5 = div_small<C>(ms5, C(6), C(1.0 / 6.0));
+  const C r6 = div_small<C>(ms6, C(12), C(1.0 / 12.0));
   const C r7 = ms7 * C(0.25), r8 = ms8 * C(0.25);
   const C ax = r0 - r1 - C(2) * r2;  // common part of i = 1..4
   const C dg = r0 + C(2) * r1 + r2;  // common part of i = 5..8
@@ -193,20 +252,19 @@ __device__ __forceinline__ void collide(const NodeParams<C>& P, const Macro<C>& 
   f[8] = dg + qx - qy - r8;
 
   // ---- temperatures
-  const C Srf = m.a * (m.dTs - m.dTf) + P.qf;  // Eq. 42
-  const C Srs = m.b * (m.dTf - m.dTs) + P.qs;
+  const C Srf = m.Srf, Srs = m.Srs;  // Eq. 42
   {
     const C Tf = P.T0 + m.dTf;
     const C n1 = gf[1] - gf[3], n2 = gf[2] - gf[4];
     const C n3 = C(-4) * gf[0] + ((gf[1] + gf[2]) + (gf[3] + gf[4]));
     const C n4 = (gf[1] - gf[2]) + (gf[3] - gf[4]);
-    const C ns0 = m.dTf + C(0.5) * Srf;
+    const C ns0 = m.sgf + Srf;  // = T_f + Sr_f / 2 (Eq. 41)
     const C ns1 = n1 - P.zeta_a * (n1 - ux * Tf * ip);
     const C ns2 = n2 - P.zeta_a * (n2 - uy * Tf * ip);
     const C ns3 = n3 - P.zeta_e * (n3 - P.c3 * m.dTf) + (C(1) - C(0.5) * P.zeta_e) * P.c3 * Srf;
     const C ns4 = n4 - P.zeta_nu * n4;
-    const C t0 = ns0 * C(0.2), t1 = ns1 * C(0.5), t2 = ns2 * C(0.5);
-    const C t3 = ns3 * C(0.05), t4 = ns4 * C(0.25);
+    const C t0 = div_small<C>(ns0, C(5), C(0.2)), t1 = ns1 * C(0.5), t2 = ns2 * C(0.5);
+    const C t3 = div_small<C>(ns3, C(20), C(0.05)), t4 = ns4 * C(0.25);
     gf[0] = t0 - C(4) * t3;
     gf[1] = t0 + t1 + t3 + t4;
     gf[2] = t0 + t2 + t3 - t4;
@@ -217,13 +275,13 @@ __device__ __forceinline__ void collide(const NodeParams<C>& P, const Macro<C>& 
     const C n1 = gs[1] - gs[3], n2 = gs[2] - gs[4];
     const C n3 = C(-4) * gs[0] + ((gs[1] + gs[2]) + (gs[3] + gs[4]));
     const C n4 = (gs[1] - gs[2]) + (gs[3] - gs[4]);
-    const C ns0 = m.dTs + C(0.5) * Srs;
+    const C ns0 = m.sgs + Srs;  // = T_s + Sr_s / 2
     const C ns1 = n1 - P.eta_a * n1;
     const C ns2 = n2 - P.eta_a * n2;
     const C ns3 = n3 - P.eta_e * (n3 - P.c3 * m.dTs) + (C(1) - C(0.5) * P.eta_e) * P.c3 * Srs;
     const C ns4 = n4 - P.eta_nu * n4;
-    const C t0 = ns0 * C(0.2), t1 = ns1 * C(0.5), t2 = ns2 * C(0.5);
-    const C t3 = ns3 * C(0.05), t4 = ns4 * C(0.25);
+    const C t0 = div_small<C>(ns0, C(5), C(0.2)), t1 = ns1 * C(0.5), t2 = ns2 * C(0.5);
+    const C t3 = div_small<C>(ns3, C(20), C(0.05)), t4 = ns4 * C(0.25);
     gs[0] = t0 - C(4) * t3;
     gs[1] = t0 + t1 + t3 + t4;
     gs[2] = t0 + t2 + t3 - t4;
@@ -240,7 +298,7 @@ __device__ __forceinline__ void collide(const NodeParams<C>& P, const Macro<C>& 
 //   gs_b = w~ T_w  + (gs_n - w~ T_s,n)                       (Eq. 51)
 // dTwf, dTws are the wall temperatures minus T0 for the two phases.
 template <typename C>
-__device__ __forceinline__ void nee(const NodeParams<C>& P, const Macro<C>& mn, C dTwf, C dTws,
+LTNE_HD void nee(const NodeParams<C>& P, const Macro<C>& mn, C dTwf, C dTws,
                                     C (&f)[9], C (&gf)[5], C (&gs)[5]) {
   const C ux = mn.ux, uy = mn.uy, ip = mn.inv_phi, rho = mn.rho;
   // f^eq(rho,u,phi) - w rho = w rho [3 e.u + 4.5 (e.u)^2/phi - 1.5 u^2/phi] (Eq. 24)
@@ -274,11 +332,13 @@ __device__ __forceinline__ void nee(const NodeParams<C>& P, const Macro<C>& mn, 
 }
 
 // Equilibrium deviations of given fields (Eqs. 24, 50, 51), for S_0.
+// drho = rho - rho0, dTf = T_f - T0, dTs = T_s - T0.
 template <typename C>
-__device__ __forceinline__ void equilibrium(const NodeParams<C>& P, C phi, C rho, C ux, C uy,
-                                            C Tf, C Ts, C (&f)[9], C (&gf)[5], C (&gs)[5]) {
+LTNE_HD void equilibrium(const NodeParams<C>& P, C phi, C drho, C ux, C uy,
+                                            C dTf, C dTs, C (&f)[9], C (&gf)[5], C (&gs)[5]) {
   const C ip = C(1) / phi;
-  const C drho = rho - P.rho0;
+  const C rho = P.rho0 + drho;
+  const C Tf = P.T0 + dTf;
   const C q = C(1.5) * (ux * ux + uy * uy) * ip;
   const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w2 = C(1.0 / 36.0);
   const C e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
@@ -291,7 +351,6 @@ __device__ __forceinline__ void equilibrium(const NodeParams<C>& P, C phi, C rho
   f[6] = w2 * drho + w2 * rho * (C(3) * e6 + C(4.5) * e6 * e6 * ip - q);
   f[7] = w2 * drho + w2 * rho * (C(-3) * e5 + C(4.5) * e5 * e5 * ip - q);
   f[8] = w2 * drho + w2 * rho * (C(-3) * e6 + C(4.5) * e6 * e6 * ip - q);
-  const C dTf = Tf - P.T0, dTs = Ts - P.T0;
   const C hx = C(0.5) * ux * Tf * ip, hy = C(0.5) * uy * Tf * ip;
   gf[0] = P.wt0 * dTf;
   gf[1] = P.wt1 * dTf + hx;
@@ -306,29 +365,74 @@ __device__ __forceinline__ void equilibrium(const NodeParams<C>& P, C phi, C rho
 }
 
 // ---- storage codec: deviation <-> stored value
+//
+// The 16-bit forms round stochastically: a stored value is rounded up with
+// probability equal to its distance from the value below, so the rounding
+// error has zero mean.  Round-to-nearest would drop every per-step change
+// smaller than half a unit in the last place, always in the same direction
+// (stagnation), which at large lattices is most of the diffusion.  The random
+// bits come from a counter-based stream keyed by (node, step); each value
+// takes 16 of them.
+
+// MurmurHash3's 32-bit finaliser (fmix32).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Marsaglia's xorshift32 stream seeded from fmix32(node ^ fmix32(step)).
+struct RandomBits {
+  uint32_t s;
+  __device__ __forceinline__ RandomBits(uint32_t node, uint32_t step)
+      : s(fmix32(node ^ fmix32(step * 0x9e3779b9u + 0x7f4a7c15u)) | 1u) {}
+  __device__ __forceinline__ uint32_t next() {
+    s ^= s << 13;
+    s ^= s >> 17;
+    s ^= s << 5;
+    return s;
+  }
+};
+
 template <typename S, typename C> struct Codec;
 template <> struct Codec<double, double> {
+  static constexpr bool kStochastic = false;
   static __device__ __forceinline__ double dec(double v, double) { return v; }
-  static __device__ __forceinline__ double enc(double v, double) { return v; }
+  static __device__ __forceinline__ double enc(double v, double, uint32_t) { return v; }
 };
 template <> struct Codec<float, float> {
+  static constexpr bool kStochastic = false;
   static __device__ __forceinline__ float dec(float v, float) { return v; }
-  static __device__ __forceinline__ float enc(float v, float) { return v; }
+  static __device__ __forceinline__ float enc(float v, float, uint32_t) { return v; }
 };
 template <> struct Codec<__half, float> {
+  static constexpr bool kStochastic = true;
   static __device__ __forceinline__ float dec(__half v, float inv_scale) {
     return __half2float(v) * inv_scale;
   }
-  static __device__ __forceinline__ __half enc(float v, float scale) {
-    return __float2half_rn(v * scale);
+  // The deviation is scaled by 2^10 (exact) so that values down to ~6e-8
+  // stay in the normal FP16 range.  FP32 keeps 23 fraction bits and FP16 10:
+  // add 13 random bits below the kept ones and truncate, then convert (exact
+  // for normal FP16 values).  Fewer random bits would quantise the round-up
+  // probability, itself a bias for increments far below an ulp.
+  static __device__ __forceinline__ __half enc(float v, float scale, uint32_t r) {
+    uint32_t b = __float_as_uint(v * scale);
+    b = (b + (r & 0x1fffu)) & ~0x1fffu;
+    return __float2half_rn(__uint_as_float(b));
   }
 };
 template <> struct Codec<__nv_bfloat16, float> {
-  static __device__ __forceinline__ float dec(__nv_bfloat16 v, float inv_scale) {
-    return __bfloat162float(v) * inv_scale;
+  static constexpr bool kStochastic = true;
+  static __device__ __forceinline__ float dec(__nv_bfloat16 v, float) {
+    return __bfloat162float(v);
   }
-  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float scale) {
-    return __float2bfloat16_rn(v * scale);
+  // BF16 is the top half of FP32: add 16 random bits and truncate.
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float, uint32_t r) {
+    const uint32_t b = __float_as_uint(v) + (r & 0xffffu);
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
   }
 };
 

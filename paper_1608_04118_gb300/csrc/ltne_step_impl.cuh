@@ -35,6 +35,9 @@ __host__ NodeParams<C> cast_params(const NodeParams<double>& d) {
   p.nu_over_K = C(d.nu_over_K); p.inv_sqrtK = C(d.inv_sqrtK); p.Fconst = C(d.Fconst);
   p.erg_a = C(d.erg_a); p.erg_b = C(d.erg_b); p.erg_c = C(d.erg_c);
   p.kmode = d.kmode; p.fmode = d.fmode;
+  p.um.phi = C(d.um.phi); p.um.inv_phi = C(d.um.inv_phi); p.um.a = C(d.um.a);
+  p.um.b = C(d.um.b); p.um.inv_1d = C(d.um.inv_1d); p.um.c0 = C(d.um.c0);
+  p.um.c1 = C(d.um.c1); p.um.l0 = C(d.um.l0); p.um.l1 = C(d.um.l1);
   return p;
 }
 
@@ -66,41 +69,57 @@ struct Pops {
       gs[i] = Codec<S, C>::dec(src[(int64_t)(14 + i) * plane + src_off[i]], inv_scale);
   }
 
+  // Writes the 19 post-collision deviations of the node at offset off.
+  // seed_node / seed_step key the stochastic rounding of the 16-bit forms.
   static __device__ __forceinline__ void store(S* __restrict__ dst, int64_t plane, int64_t off,
                                                C scale, const C (&f)[9], const C (&gf)[5],
-                                               const C (&gs)[5]) {
+                                               const C (&gs)[5], uint32_t seed_node,
+                                               uint32_t seed_step) {
+    if constexpr (Codec<S, C>::kStochastic) {
+      RandomBits rb(seed_node, seed_step);
+      uint32_t r = 0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) dst[(int64_t)i * plane + off] = Codec<S, C>::enc(f[i], scale);
+      for (int i = 0; i < 19; ++i) {
+        if ((i & 1) == 0) r = rb.next();
+        const uint32_t ri = (i & 1) ? (r >> 16) : r;
+        const C v = i < 9 ? f[i] : (i < 14 ? gf[i - 9] : gs[i - 14]);
+        dst[(int64_t)i * plane + off] = Codec<S, C>::enc(v, scale, ri);
+      }
+    } else {
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
-      dst[(int64_t)(9 + i) * plane + off] = Codec<S, C>::enc(gf[i], scale);
+      for (int i = 0; i < 9; ++i) dst[(int64_t)i * plane + off] = Codec<S, C>::enc(f[i], scale, 0);
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
-      dst[(int64_t)(14 + i) * plane + off] = Codec<S, C>::enc(gs[i], scale);
+      for (int i = 0; i < 5; ++i)
+        dst[(int64_t)(9 + i) * plane + off] = Codec<S, C>::enc(gf[i], scale, 0);
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        dst[(int64_t)(14 + i) * plane + off] = Codec<S, C>::enc(gs[i], scale, 0);
+    }
   }
 };
 
+// The macro planes hold deviations (rho - rho0, ux, uy, T_f - T0, T_s - T0)
+// so that FP32 keeps its full relative precision on them; the host adds the
+// references back in FP64.
 template <typename C>
 __device__ __forceinline__ void store_macros(C* __restrict__ mac, int64_t plane, int64_t off,
-                                             const NodeParams<C>& P, const Macro<C>& m) {
-  mac[off] = m.rho;
+                                             const Macro<C>& m) {
+  mac[off] = m.drho;
   mac[plane + off] = m.ux;
   mac[2 * plane + off] = m.uy;
-  mac[3 * plane + off] = P.T0 + m.dTf;
-  mac[4 * plane + off] = P.T0 + m.dTs;
+  mac[3 * plane + off] = m.dTf;
+  mac[4 * plane + off] = m.dTs;
 }
 
+// One node (x, y) of one time step: pull, wall rebuild, macroscopic values,
+// collision, store.  Shared by the single-lattice and the batched kernels.
 template <typename S, typename C, int BC>
-__global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst,
-                                              const C* __restrict__ phi_field,
-                                              C* __restrict__ mac, const NodeParams<C> P,
-                                              const int nx, const int ny, const int64_t pitch,
-                                              const int64_t plane, const C scale,
-                                              const C inv_scale, const int write_macros) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= nx || y >= ny) return;
-
+__device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restrict__ dst,
+                                          const C* __restrict__ phi_field, C* __restrict__ mac,
+                                          const NodeParams<C>& P, const int x, const int y,
+                                          const int nx, const int ny, const int64_t pitch,
+                                          const int64_t plane, const C scale, const C inv_scale,
+                                          const int write_macros, const uint32_t tick) {
   // Wall classification and the node whose neighbourhood is pulled.
   int cx = x, cy = y;
   int kind = -1;  // -1 interior, 0 hot wall, 1 cold wall, 2 adiabatic / no-slip row
@@ -135,20 +154,52 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
 
   const int64_t off = (int64_t)y * pitch + x;
   if (BC != BC_PERIODIC && kind >= 0) {
-    const C phin = phi_field ? phi_field[(int64_t)cy * pitch + cx] : P.phi_u;
+    const Medium<C> mdn = phi_field ? medium_at<C>(P, phi_field[(int64_t)cy * pitch + cx]) : P.um;
     Macro<C> mn;
-    macros<C>(P, phin, f, gf, gs, mn);
+    macros<C>(P, mdn, f, gf, gs, mn);
     C dTwf = mn.dTf, dTws = mn.dTs;  // adiabatic: the neighbour's temperature
     if (kind == 0) dTwf = dTws = P.dT_hot;
     if (kind == 1) dTwf = dTws = P.dT_cold;
     nee<C>(P, mn, dTwf, dTws, f, gf, gs);
   }
-  const C phi = phi_field ? phi_field[off] : P.phi_u;
+  const Medium<C> md = phi_field ? medium_at<C>(P, phi_field[off]) : P.um;
   Macro<C> m;
-  macros<C>(P, phi, f, gf, gs, m);
-  if (write_macros) store_macros<C>(mac, plane, off, P, m);
+  macros<C>(P, md, f, gf, gs, m);
+  if (write_macros) store_macros<C>(mac, plane, off, m);
   collide<C>(P, m, f, gf, gs);
-  Pops<S, C>::store(dst, plane, off, scale, f, gf, gs);
+  Pops<S, C>::store(dst, plane, off, scale, f, gf, gs, (uint32_t)off, tick);
+}
+
+// Step counter of the stochastic rounding: every thread reads one slot and
+// one thread writes the next value to the other (the slots alternate with
+// the A-B buffers, so no slot is read and written by the same launch).
+template <typename S, typename C>
+__device__ __forceinline__ uint32_t read_tick(const uint32_t* __restrict__ tick_in,
+                                              uint32_t* __restrict__ tick_out) {
+  uint32_t tick = 0;
+  if constexpr (Codec<S, C>::kStochastic) {
+    tick = *tick_in;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+      *tick_out = tick + 1u;
+  }
+  return tick;
+}
+
+template <typename S, typename C, int BC>
+__global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst,
+                                              const C* __restrict__ phi_field,
+                                              C* __restrict__ mac, const NodeParams<C> P,
+                                              const int nx, const int ny, const int64_t pitch,
+                                              const int64_t plane, const C scale,
+                                              const C inv_scale, const int write_macros,
+                                              const uint32_t* __restrict__ tick_in,
+                                              uint32_t* __restrict__ tick_out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const uint32_t tick = read_tick<S, C>(tick_in, tick_out);
+  if (x >= nx || y >= ny) return;
+  step_node<S, C, BC>(src, dst, phi_field, mac, P, x, y, nx, ny, pitch, plane, scale, inv_scale,
+                      write_macros, tick);
 }
 
 // S_0 from the fields held in the macro planes (rho, ux, uy, Tf, Ts), then
@@ -163,15 +214,15 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ dst,
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int64_t off = (int64_t)y * pitch + x;
-  const C phi = phi_field ? phi_field[off] : P.phi_u;
+  const Medium<C> md = phi_field ? medium_at<C>(P, phi_field[off]) : P.um;
   C f[9], gf[5], gs[5];
-  equilibrium<C>(P, phi, mac[off], mac[plane + off], mac[2 * plane + off], mac[3 * plane + off],
-                 mac[4 * plane + off], f, gf, gs);
+  equilibrium<C>(P, md.phi, mac[off], mac[plane + off], mac[2 * plane + off],
+                 mac[3 * plane + off], mac[4 * plane + off], f, gf, gs);
   Macro<C> m;
-  macros<C>(P, phi, f, gf, gs, m);
-  store_macros<C>(mac, plane, off, P, m);
+  macros<C>(P, md, f, gf, gs, m);
+  store_macros<C>(mac, plane, off, m);
   collide<C>(P, m, f, gf, gs);
-  Pops<S, C>::store(dst, plane, off, scale, f, gf, gs);
+  Pops<S, C>::store(dst, plane, off, scale, f, gf, gs, (uint32_t)off, 0xffffffffu);
 }
 
 template <typename S, typename C>
@@ -188,17 +239,18 @@ cudaError_t launch_step_t(const LatticeArgs& a, const NodeParams<double>& Pd, St
   switch (a.bc) {
     case BC_CAVITY:
       k_step<S, C, BC_CAVITY><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny, a.pitch,
-                                                      a.plane, scale, inv_scale, a.write_macros);
+                                                      a.plane, scale, inv_scale, a.write_macros,
+                                                      a.tick_in, a.tick_out);
       break;
     case BC_PERIODIC:
       k_step<S, C, BC_PERIODIC><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
                                                         a.pitch, a.plane, scale, inv_scale,
-                                                        a.write_macros);
+                                                        a.write_macros, a.tick_in, a.tick_out);
       break;
     case BC_CHANNEL:
       k_step<S, C, BC_CHANNEL><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
                                                        a.pitch, a.plane, scale, inv_scale,
-                                                       a.write_macros);
+                                                       a.write_macros, a.tick_in, a.tick_out);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -89,6 +89,17 @@ SIGNATURES = {
     "ltne_launch_count": (C.c_int64, [_vp]),
     "ltne_destroy": (None, [_vp]),
     "ltne_error_string": (C.c_char_p, [C.c_int]),
+    "ltne_batch_create": (C.c_int, [C.POINTER(ltne_params), C.c_int32, _vp, C.POINTER(_vp)]),
+    "ltne_batch_workspace_bytes": (C.c_size_t, [_vp]),
+    "ltne_batch_nodes": (C.c_int64, [_vp]),
+    "ltne_batch_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "ltne_batch_set_schedule": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+    "ltne_batch_set_fields": (C.c_int, [_vp]),
+    "ltne_batch_step": (C.c_int, [_vp, C.c_int64]),
+    "ltne_batch_observables": (C.c_int, [_vp, C.POINTER(ltne_obs)]),
+    "ltne_batch_get_fields": (C.c_int, [_vp, C.c_int32, _dp, _dp, _dp, _dp, _dp]),
+    "ltne_batch_launch_count": (C.c_int64, [_vp]),
+    "ltne_batch_destroy": (None, [_vp]),
 }
 
 
@@ -273,6 +284,136 @@ class Cavity:
         if getattr(self, "h", None):
             ltne_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched form -----------------------------------------------------------
+
+def ltne_batch_create(params_list, stream=None):
+    arr = (ltne_params * len(params_list))(*params_list)
+    h = _vp()
+    s = _vp(int(stream) if stream is not None else 0)
+    _check(_lib().ltne_batch_create(arr, len(params_list), s, C.byref(h)), "ltne_batch_create")
+    return h
+
+
+def ltne_batch_workspace_bytes(b) -> int:
+    return int(_lib().ltne_batch_workspace_bytes(b))
+
+
+def ltne_batch_nodes(b) -> int:
+    return int(_lib().ltne_batch_nodes(b))
+
+
+def ltne_batch_bind_workspace(b, device_ptr: int, nbytes: int):
+    _check(_lib().ltne_batch_bind_workspace(b, _vp(int(device_ptr)), int(nbytes)),
+           "ltne_batch_bind_workspace")
+
+
+def ltne_batch_set_schedule(b, tile_x, tile_y, blocks):
+    _check(_lib().ltne_batch_set_schedule(b, int(tile_x), int(tile_y), int(blocks)),
+           "ltne_batch_set_schedule")
+
+
+def ltne_batch_set_fields(b):
+    _check(_lib().ltne_batch_set_fields(b), "ltne_batch_set_fields")
+
+
+def ltne_batch_step(b, n):
+    _check(_lib().ltne_batch_step(b, int(n)), "ltne_batch_step")
+
+
+def ltne_batch_observables(b, count, allow_nonfinite=False):
+    out = (ltne_obs * count)()
+    rc = _lib().ltne_batch_observables(b, out)
+    if not (rc == LTNE_OK or (allow_nonfinite and rc == LTNE_ERR_NONFINITE)):
+        raise LtneError(rc, "ltne_batch_observables")
+    return [o.as_dict() for o in out]
+
+
+def ltne_batch_get_fields(b, index, nx, ny):
+    out = {k: np.empty(nx * ny) for k in ("rho", "ux", "uy", "Tf", "Ts")}
+    _check(_lib().ltne_batch_get_fields(b, int(index),
+                                        *[_ptr(out[k]) for k in ("rho", "ux", "uy", "Tf", "Ts")]),
+           "ltne_batch_get_fields")
+    return {k: v.reshape(ny, nx) for k, v in out.items()}
+
+
+def ltne_batch_launch_count(b) -> int:
+    return int(_lib().ltne_batch_launch_count(b))
+
+
+def ltne_batch_destroy(b):
+    if b:
+        _lib().ltne_batch_destroy(b)
+
+
+class Batch:
+    """Many independent FP32 cavities advanced together on one device.
+
+    ``Batch([dict(nx=.., ny=.., Ra=.., ...), ...])``: each dict takes
+    ltne_params fields (storage, bc and porosity_field are fixed)."""
+
+    def __init__(self, cavities, stream=None, device=None):
+        import torch
+
+        self.shapes = [(int(c["nx"]), int(c["ny"])) for c in cavities]
+        plist = []
+        for c in cavities:
+            kw = {k: v for k, v in c.items() if k not in ("nx", "ny")}
+            plist.append(ltne_default_params(c["nx"], c["ny"], storage=LTNE_F32, **kw))
+        dev = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        self.b = ltne_batch_create(plist, stream.cuda_stream)
+        nbytes = ltne_batch_workspace_bytes(self.b)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        ltne_batch_bind_workspace(self.b, self.workspace.data_ptr(), nbytes)
+        self.schedule = (128, 2, 0)
+
+    @property
+    def count(self):
+        return len(self.shapes)
+
+    @property
+    def nodes(self):
+        return ltne_batch_nodes(self.b)
+
+    def set_schedule(self, tile_x, tile_y, blocks):
+        ltne_batch_set_schedule(self.b, tile_x, tile_y, blocks)
+        self.schedule = (tile_x, tile_y, blocks)
+        return self
+
+    def set_fields(self):
+        ltne_batch_set_fields(self.b)
+        return self
+
+    def step(self, n):
+        ltne_batch_step(self.b, n)
+        return self
+
+    def observables(self, allow_nonfinite=False):
+        return ltne_batch_observables(self.b, self.count, allow_nonfinite)
+
+    def fields(self, index):
+        nx, ny = self.shapes[index]
+        return ltne_batch_get_fields(self.b, index, nx, ny)
+
+    @property
+    def launches(self):
+        return ltne_batch_launch_count(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            ltne_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
