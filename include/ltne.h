@@ -182,6 +182,38 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes);
 /* Number of step-kernel launches issued by this handle so far. */
 int64_t ltne_launch_count(const ltne_handle* h);
 
+/* Observables of fields the caller holds on the device, allocating nothing.
+   The paper has no counterpart: this serves callers that cannot allocate
+   device memory at the moment they need a reduction -- code running inside
+   CUDA graph capture (allocation is not allowed there), a framework whose
+   allocator is not reachable from the calling thread, a loop that must not
+   allocate.  Those callers can neither size nor bind a workspace, so the
+   reduction's per-block partial sums go to a fixed __device__ array inside
+   this library (590 KB, held by every GPU that loads the library until the
+   process exits).
+   fields: device, FP32, five planes of nx*ny values with row pitch `pitch`
+     (>= nx) elements and plane stride pitch*ny, holding rho - 1, u_x, u_y,
+     T_f - T_ref, T_s - T_ref (the layout ltne_get_fields() values map to).
+   porosity: device, FP32, one plane in the same layout, non-NULL iff
+     p->porosity_field; otherwise p->porosity is used.
+   step: reported in out->step and used for out->Fo.
+   p: the problem statement (validated as by ltne_create; storage must not
+     be LTNE_F64).  Results equal ltne_observables() on the same fields,
+     except that no residual snapshot is kept: out->residual is NaN.
+   Limit: ceil(nx/256) * ceil(ny/64) <= 4096 (e.g. any lattice up to
+     8192 x 8192); larger lattices return LTNE_ERR_INVALID_ARG before any
+     device work.
+   The first call on each device asks the runtime for the array's device
+   address (cudaGetSymbolAddress, with that device current), so make one
+   call before any stream capture begins.  All calls share the array and it
+   keeps the last call's contents (every slot a call reads is written by that
+   call first): calls that overlap on the GPU -- on different streams, or on
+   one stream while another thread also calls -- race and give wrong
+   results.  Synchronises `cuda_stream`. */
+int ltne_observables_static(const ltne_params* p, const float* fields, int64_t pitch,
+                            const float* porosity, int64_t step, void* cuda_stream,
+                            ltne_obs* out);
+
 /* Free the handle's host state and graphs (not the workspace). */
 void ltne_destroy(ltne_handle* h);
 

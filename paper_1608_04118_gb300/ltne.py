@@ -87,6 +87,8 @@ SIGNATURES = {
     "ltne_get_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "ltne_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "ltne_launch_count": (C.c_int64, [_vp]),
+    "ltne_observables_static": (C.c_int, [C.POINTER(ltne_params), _vp, C.c_int64, _vp, C.c_int64,
+                                          _vp, C.POINTER(ltne_obs)]),
     "ltne_destroy": (None, [_vp]),
     "ltne_error_string": (C.c_char_p, [C.c_int]),
     "ltne_batch_create": (C.c_int, [C.POINTER(ltne_params), C.c_int32, _vp, C.POINTER(_vp)]),
