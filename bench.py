@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: single cavity (default, the headline line); c3: 256-cavity "
-                         "batch; c5: reduced-storage forms at 8192^2 with their errors")
+                         "batch; c4: forward + adjoint; c5: reduced-storage forms at 8192^2 "
+                         "with their errors")
     return ap.parse_args()
 
 
@@ -356,6 +357,62 @@ def run_reduced(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Reverse-mode form: 256 x 256 cavity, porosity U[0.4, 0.8] (seed 4),
+    Ra 1e5, Da 1e-3 (Ergun), H 50; forward 4000 steps then the gradient of
+    the hot-wall Nusselt average with respect to the per-node porosity and H
+    (64-step checkpoint segments).  MLUPS = nodes x steps / (forward +
+    recompute + reverse time), next to the plain FP32 forward."""
+    import math
+
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1608_04118_gb300 import build as B
+
+    B.build()
+    from paper_1608_04118_gb300.ltne import Cavity, LTNE_K_ERGUN
+
+    c = W.C4_ADJOINT
+    nx, ny = c["nx"], c["ny"]
+    steps = args.steps if args.steps != 2000 else c["steps"]
+    seg = int(math.ceil(math.sqrt(steps)))
+    phi = W.porosity_field(nx, ny, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+    kw = {k: c[k] for k in ("Ra", "Pr", "Da", "H", "gamma_sf", "sigma", "T_hot", "T_cold",
+                            "T_ref")}
+    stream = torch.cuda.Stream()
+    cav = Cavity(nx, ny, stream=stream, storage="f32", permeability=LTNE_K_ERGUN,
+                 porosity_field=1, **kw)
+    cav.adjoint(phi, 64, segment=8)  # warm-up (kernels loaded, allocator primed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, g, dH = cav.adjoint(phi, steps, segment=seg)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    cav.set_fields(porosity=phi)
+    with torch.cuda.stream(stream):
+        cav.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    cav.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_fwd = ev0.elapsed_time(ev1) / 1e3
+    nodes = nx * ny
+    line = {"metric": "MLUPS (forward + adjoint, 256x256)", "value": nodes * steps / t_adj / 1e6,
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "porous LTNE cavity 256x256, porosity U[0.4,0.8] seed 4, "
+                                   "Ergun mean Da 1e-3, Ra 1e5, H 50", "segment": seg,
+                       "objective": "(Nu_f,hot + Nu_s,hot)/2 at the last step"},
+            "seconds": t_adj, "plain_forward_mlups": nodes * steps / t_fwd / 1e6,
+            "ratio_to_plain_forward": (nodes * steps / t_adj) / (nodes * steps / t_fwd),
+            "J": J, "dJ_dH": dH, "max_abs_dJ_dphi": float(g.abs().max())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -363,6 +420,9 @@ def main():
         return
     if args.workload == "c3":
         run_batch(args)
+        return
+    if args.workload == "c4":
+        run_adjoint(args)
         return
     if args.workload == "c5":
         run_reduced(args)

@@ -182,6 +182,36 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes);
 /* Number of step-kernel launches issued by this handle so far. */
 int64_t ltne_launch_count(const ltne_handle* h);
 
+/* ------------------------------------------------------------------------
+ * Adjoint: gradients of J = (Nu_f,hot + Nu_s,hot) / 2 after n_steps steps
+ * with respect to the per-node porosity and to H, by hand-written reverse
+ * kernels of the time step (transposed collision, streaming and wall
+ * rebuild of Sec. 3 / Sec. 4) with checkpoints every `segment` steps.  The
+ * Ergun particle diameter derived from the porosity field is held fixed.
+ * Restrictions: bc LTNE_BC_CAVITY, porosity_field = 1, storage LTNE_F32 or
+ * LTNE_F64 (the gradient is computed in that precision), T_hot != T_cold,
+ * and the fluid initially at rest (no initial velocity), which makes the
+ * initial state independent of the porosity and of H.
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of the adjoint workspace (caller-owned device memory): checkpoints
+   of the pre-collision state at every segment start, `segment` recompute
+   slots, adjoint and gradient buffers; about
+   (ceil(n_steps/segment) + segment + 4) * 19 planes of the compute type. */
+size_t ltne_adjoint_workspace_bytes(const ltne_handle* h, int64_t n_steps, int32_t segment);
+
+/* Set the initial fields (as ltne_set_fields with u = 0; rho, T_f, T_s may
+   be NULL), run n_steps >= 1 steps forward (the handle ends at step
+   n_steps, exactly as after ltne_step), compute *J, and by the reverse
+   sweep dJ/dphi into dJ_dphi (device, nx*ny values of the compute type,
+   row-major, may be NULL) and dJ/dH into *dJ_dH.  adj_workspace: device,
+   >= ltne_adjoint_workspace_bytes(), 256-byte aligned.  Synchronises the
+   handle's stream.  Errors: INVALID_ARG (restrictions above, bad sizes),
+   WORKSPACE, STATE (no workspace bound), CUDA. */
+int ltne_adjoint(ltne_handle* h, const double* porosity, const double* rho, const double* T_f,
+                 const double* T_s, int64_t n_steps, int32_t segment, void* adj_workspace,
+                 size_t bytes, void* dJ_dphi, double* J, double* dJ_dH);
+
 /* Observables of fields the caller holds on the device, allocating nothing.
    The paper has no counterpart: this serves callers that cannot allocate
    device memory at the moment they need a reduction -- code running inside

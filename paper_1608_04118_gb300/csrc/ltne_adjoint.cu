@@ -1,0 +1,431 @@
+// ltne_adjoint.cu -- reverse-mode (adjoint) time stepping of the
+// three-distribution MRT-LB method (Liu & He, arXiv:1608.04118) for
+// gradients of J = (Nu_f,hot + Nu_s,hot)/2 at the final step with respect to
+// the per-node porosity and to H.
+//
+// State: S_n = pre-collision populations after streaming and the wall
+// rebuild.  One forward transition is S_{n+1} = W(Pull(Coll(S_n))), Coll the
+// per-node collision (Eqs. 10, 32, 33 with Eqs. 5-7, 15, 37-46), Pull the
+// streaming (Eqs. 11, 34, 35) and W the wall rebuild.  Its transpose, applied
+// to the adjoint lambda_{n+1} of S_{n+1}:
+//   R1 (ring kernel): every wall node's adjoint is folded onto its interior
+//      neighbour through the transposed wall-rebuild Jacobian, then zeroed;
+//      one thread per neighbour (each wall node has exactly one), no atomics.
+//   R2 (grid kernel): the adjoint of Coll's output at y is gathered from
+//      y + e_i (the transpose of a pull is a pull the other way; only
+//      interior targets pulled), then the transposed collision Jacobian at
+//      S_n(y) gives lambda_n(y) and the porosity / h_v contributions.
+// Gradients accumulate per node (porosity, and the h_v term reduced once in
+// FP64 at the end), so the result is deterministic.
+//
+// Memory: sqrt(T)-style checkpointing.  The forward pass records S_a at the
+// start of every segment of K steps; the reverse sweep recomputes each
+// segment's S_{a+1..a+K} from its checkpoint into K slots, then walks back
+// through it.  Total extra work: one forward pass.
+#include <math.h>
+#include <string.h>
+
+#include "ltne.h"
+#include "ltne_internal.h"
+#include "ltne_step_impl.cuh"
+#include "ltne_adjoint.cuh"
+
+using namespace ltne;
+
+namespace {
+
+constexpr int kRB = 256;
+
+template <typename C>
+__device__ __forceinline__ void load19(const C* __restrict__ b, int64_t plane, int64_t off,
+                                       C (&f)[9], C (&gf)[5], C (&gs)[5]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = b[(int64_t)i * plane + off];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) gf[i] = b[(int64_t)(9 + i) * plane + off];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) gs[i] = b[(int64_t)(14 + i) * plane + off];
+}
+
+template <typename C>
+__device__ __forceinline__ void store19(C* __restrict__ b, int64_t plane, int64_t off,
+                                        const C (&f)[9], const C (&gf)[5], const C (&gs)[5]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) b[(int64_t)i * plane + off] = f[i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) b[(int64_t)(9 + i) * plane + off] = gf[i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) b[(int64_t)(14 + i) * plane + off] = gs[i];
+}
+
+// Forward step that also records S_{n+1} (pre_out may be null).
+template <typename C>
+__global__ void __launch_bounds__(256) k_step_record(const C* __restrict__ src,
+                                                     C* __restrict__ dst,
+                                                     const C* __restrict__ phi,
+                                                     C* __restrict__ mac, const NodeParams<C> P,
+                                                     int nx, int ny, int64_t pitch,
+                                                     int64_t plane, int write_macros,
+                                                     C* __restrict__ pre_out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  step_node<C, C, BC_CAVITY>(src, dst, phi, mac, P, x, y, nx, ny, pitch, plane, C(1), C(1),
+                             write_macros, 0u, pre_out);
+}
+
+// Post-collision values of a recorded pre-collision state.
+template <typename C>
+__global__ void __launch_bounds__(256) k_collide_pre(const C* __restrict__ pre,
+                                                     C* __restrict__ dst,
+                                                     const C* __restrict__ phi,
+                                                     const NodeParams<C> P, int nx, int ny,
+                                                     int64_t pitch, int64_t plane) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const int64_t off = (int64_t)y * pitch + x;
+  C f[9], gf[5], gs[5];
+  load19(pre, plane, off, f, gf, gs);
+  const Medium<C> md = medium_at<C>(P, phi[off]);
+  Macro<C> m;
+  macros<C>(P, md, f, gf, gs, m);
+  collide<C>(P, m, f, gf, gs);
+  store19(dst, plane, off, f, gf, gs);
+}
+
+// lambda_N: J depends on S_N through the temperatures of columns 1 and 2
+// (wall-flux stencil of the Nusselt numbers, trapezoid weights in y).
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_seed(const C* __restrict__ SN, C* __restrict__ lam,
+                                                  const C* __restrict__ phi,
+                                                  C* __restrict__ phib, C* __restrict__ hb,
+                                                  const NodeParams<C> P, int nx, int ny,
+                                                  int64_t pitch, int64_t plane, C inv_dT) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * ny) return;
+  const int y = t >> 1, x = 1 + (t & 1);
+  const int64_t off = (int64_t)y * pitch + x;
+  const C wy = (y == 0 || y == ny - 1) ? C(0.5) : C(1);
+  // J = (1/2)(Nu_f + Nu_s), Nu = (1/dT) sum_y w_y (1.5 T_h - 2 T(1,y) + 0.5 T(2,y))
+  const C dT_b = (x == 1) ? -wy * inv_dT : C(0.25) * wy * inv_dT;
+  C f[9], gf[5], gs[5];
+  load19(SN, plane, off, f, gf, gs);
+  const C ph = phi[off];
+  const Medium<C> md = medium_at<C>(P, ph);
+  MacroBar<C> mb;
+  zero(mb);
+  mb.dTf = dT_b;
+  mb.dTs = dT_b;
+  C fb[9] = {}, gfb[5] = {}, gsb[5] = {};
+  MediumBar<C> mdb;
+  zero(mdb);
+  macros_adjoint<C>(P, md, f, gf, gs, mb, fb, gfb, gsb, mdb);
+  store19(lam, plane, off, fb, gfb, gsb);
+  C pb = C(0), hv = C(0);
+  medium_adjoint<C>(P, ph, mdb, pb, hv);
+  phib[off] += pb;
+  hb[off] += hv;
+}
+
+// R1: fold the wall nodes' adjoints onto their interior neighbours.
+// Ring of interior nodes next to a wall: rows y = 1 and y = ny-2 (all
+// interior x), then columns x = 1 and x = nx-2 for 2 <= y <= ny-3.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_wall(C* __restrict__ lam,
+                                                  const C* __restrict__ Snext,
+                                                  const C* __restrict__ phi,
+                                                  C* __restrict__ phib, C* __restrict__ hb,
+                                                  const NodeParams<C> P, int nx, int ny,
+                                                  int64_t pitch, int64_t plane) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = nx - 2, col = ny - 4;
+  int x, y;
+  if (t < row) { x = 1 + t; y = 1; }
+  else if (t < 2 * row) { x = 1 + t - row; y = ny - 2; }
+  else if (t < 2 * row + col) { x = 1; y = 2 + t - 2 * row; }
+  else if (t < 2 * row + 2 * col) { x = nx - 2; y = 2 + t - 2 * row - col; }
+  else return;
+  const int64_t off = (int64_t)y * pitch + x;
+  C L_f[9], L_gf[5], L_gs[5];
+  load19(lam, plane, off, L_f, L_gf, L_gs);
+  C f[9], gf[5], gs[5];
+  load19(Snext, plane, off, f, gf, gs);
+  const C ph = phi[off];
+  const Medium<C> md = medium_at<C>(P, ph);
+  MediumBar<C> mdb;
+  zero(mdb);
+  // wall nodes whose rebuild reads this node (isothermal columns own the corners)
+  int wx[3], wy[3];
+  bool iso[3];
+  int nw = 0;
+  if (x == 1) { wx[nw] = 0; wy[nw] = y; iso[nw] = true; ++nw; }
+  if (x == nx - 2) { wx[nw] = nx - 1; wy[nw] = y; iso[nw] = true; ++nw; }
+  if (y == 1) { wx[nw] = x; wy[nw] = 0; iso[nw] = false; ++nw; }
+  if (y == ny - 2) { wx[nw] = x; wy[nw] = ny - 1; iso[nw] = false; ++nw; }
+  const bool cx0 = (x == 1), cx1 = (x == nx - 2), cy0 = (y == 1), cy1 = (y == ny - 2);
+  int cwx[4], cwy[4], nc = 0;
+  if (cx0 && cy0) { cwx[nc] = 0; cwy[nc] = 0; ++nc; }
+  if (cx0 && cy1) { cwx[nc] = 0; cwy[nc] = ny - 1; ++nc; }
+  if (cx1 && cy0) { cwx[nc] = nx - 1; cwy[nc] = 0; ++nc; }
+  if (cx1 && cy1) { cwx[nc] = nx - 1; cwy[nc] = ny - 1; ++nc; }
+  const C zf[9] = {}, zg[5] = {};
+  for (int k = 0; k < nw + nc; ++k) {
+    const int bx = k < nw ? wx[k] : cwx[k - nw];
+    const int by = k < nw ? wy[k] : cwy[k - nw];
+    const bool isothermal = k < nw ? iso[k] : true;
+    const int64_t boff = (int64_t)by * pitch + bx;
+    C lf[9], lgf[5], lgs[5];
+    load19(lam, plane, boff, lf, lgf, lgs);
+    nee_adjoint<C>(P, md, f, gf, gs, isothermal, lf, lgf, lgs, L_f, L_gf, L_gs, mdb);
+    store19(lam, plane, boff, zf, zg, zg);  // a wall node's pulled values are unused
+  }
+  store19(lam, plane, off, L_f, L_gf, L_gs);
+  C pb = C(0), hv = C(0);
+  medium_adjoint<C>(P, ph, mdb, pb, hv);
+  phib[off] += pb;
+  hb[off] += hv;
+}
+
+// R2: transposed streaming (gather from y + e_i) and transposed collision.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_main(const C* __restrict__ Lam,
+                                                  C* __restrict__ lam_out,
+                                                  const C* __restrict__ S,
+                                                  const C* __restrict__ phi,
+                                                  C* __restrict__ phib, C* __restrict__ hb,
+                                                  const NodeParams<C> P, int nx, int ny,
+                                                  int64_t pitch, int64_t plane) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const int64_t off = (int64_t)y * pitch + x;
+  // e_i of Eq. 8
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  C qf[9], qgf[5], qgs[5];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int tx = x + ex[i], ty = y + ey[i];
+    const bool pulled = tx >= 1 && tx <= nx - 2 && ty >= 1 && ty <= ny - 2;
+    const int64_t toff = (int64_t)ty * pitch + tx;
+    qf[i] = pulled ? Lam[(int64_t)i * plane + toff] : C(0);
+    if (i < 5) {
+      qgf[i] = pulled ? Lam[(int64_t)(9 + i) * plane + toff] : C(0);
+      qgs[i] = pulled ? Lam[(int64_t)(14 + i) * plane + toff] : C(0);
+    }
+  }
+  C f[9], gf[5], gs[5];
+  load19(S, plane, off, f, gf, gs);
+  const C ph = phi[off];
+  const Medium<C> md = medium_at<C>(P, ph);
+  C fb[9] = {}, gfb[5] = {}, gsb[5] = {};
+  MediumBar<C> mdb;
+  zero(mdb);
+  collide_adjoint<C>(P, md, f, gf, gs, qf, qgf, qgs, fb, gfb, gsb, mdb);
+  store19(lam_out, plane, off, fb, gfb, gsb);
+  C pb = C(0), hv = C(0);
+  medium_adjoint<C>(P, ph, mdb, pb, hv);
+  phib[off] += pb;
+  hb[off] += hv;
+}
+
+// FP64 sum of one plane (fixed grid and order: deterministic).
+template <typename C>
+__global__ void __launch_bounds__(kRB) k_sum_plane(const C* __restrict__ v, int nx, int ny,
+                                                   int64_t pitch, double* __restrict__ part) {
+  __shared__ double sh[kRB / 32];
+  double acc = 0.0;
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = (int64_t)blockIdx.x * kRB + threadIdx.x; k < n; k += (int64_t)gridDim.x * kRB) {
+    const int y = (int)(k / nx), x = (int)(k - (int64_t)y * nx);
+    acc += (double)v[(int64_t)y * pitch + x];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kRB / 32; ++w) s += sh[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+constexpr int kSumBlocks = 128;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct AdjLayout {
+  int64_t nseg = 0;
+  size_t p19 = 0, pl = 0;  // bytes of 19 planes, of one plane
+  size_t ckpt = 0, slots = 0, pops = 0, lam = 0, phib = 0, hb = 0, part = 0, total = 0;
+};
+
+AdjLayout adj_layout(const ltne_handle* h, int64_t n_steps, int32_t segment) {
+  AdjLayout L;
+  const size_t A = 256;
+  L.nseg = (n_steps + segment - 1) / segment;
+  L.pl = align_up((size_t)h->plane * h->ec, A);
+  L.p19 = 19 * L.pl;
+  size_t off = 0;
+  L.ckpt = off;
+  off += (size_t)L.nseg * L.p19;
+  L.slots = off;
+  off += (size_t)segment * L.p19;
+  L.pops = off;
+  off += 2 * L.p19;
+  L.lam = off;
+  off += 2 * L.p19;
+  L.phib = off;
+  off += L.pl;
+  L.hb = off;
+  off += L.pl;
+  L.part = off;
+  off += align_up((kSumBlocks + 1) * sizeof(double), A);
+  L.total = off;
+  return L;
+}
+
+template <typename C>
+int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const double* T_f,
+                const double* T_s, int64_t N, int32_t K, char* ws, void* dJ_dphi, double* J,
+                double* dJ_dH) {
+  const AdjLayout L = adj_layout(h, N, K);
+  const cudaStream_t st = h->stream;
+  const int nx = h->p.nx, ny = h->p.ny;
+  const int64_t pitch = h->pitch, plane = h->plane;
+  // plane strides in elements: every buffer uses the population layout
+  const int64_t pe = (int64_t)(L.pl / sizeof(C));
+  auto buf19 = [&](size_t base, int64_t k) { return reinterpret_cast<C*>(ws + base + k * L.p19); };
+  C* phib = reinterpret_cast<C*>(ws + L.phib);
+  C* hb = reinterpret_cast<C*>(ws + L.hb);
+  double* part = reinterpret_cast<double*>(ws + L.part);
+  (void)pe;
+
+  int rc = set_fields_impl(h, porosity, rho, nullptr, nullptr, T_f, T_s, buf19(L.ckpt, 0));
+  if (rc != LTNE_OK) return rc;
+  const NodeParams<C> P = cast_params<C>(h->P);
+  const C* phi = reinterpret_cast<const C*>(h->ws + h->off_phi);
+  C* mac = reinterpret_cast<C*>(h->ws + h->off_mac);
+  const dim3 blk(128, 2), grd((nx + 127) / 128, (ny + 1) / 2);
+  cudaError_t e = cudaSuccess;
+
+  // ---- forward, recording S at the start of every segment
+  for (int64_t n = 0; n < N && e == cudaSuccess; ++n) {
+    const int64_t a = n + 1;
+    C* rec = (a % K == 0 && a < N) ? buf19(L.ckpt, a / K) : nullptr;
+    const C* src = reinterpret_cast<const C*>(h->ws + h->off_pop[h->cur]);
+    C* dst = reinterpret_cast<C*>(h->ws + h->off_pop[h->cur ^ 1]);
+    k_step_record<C><<<grd, blk, 0, st>>>(src, dst, phi, mac, P, nx, ny, pitch, plane,
+                                          n == N - 1 ? 1 : 0, rec);
+    e = cudaGetLastError();
+    h->cur ^= 1;
+    ++h->step;
+    ++h->launches;
+  }
+  if (e != cudaSuccess) return LTNE_ERR_CUDA;
+  double acc[NACC];
+  rc = reduce_handle(h, acc);
+  if (rc != LTNE_OK) return rc;
+  DerivedInfo info;
+  info.L = h->L;
+  info.nu_f = h->nu_f;
+  info.alpha_f = h->alpha_f;
+  ltne_obs ob;
+  finish_observables(h->p, info, h->step, false, acc, &ob);
+  h->have_prev = true;
+  *J = 0.5 * (ob.Nu_f_hot + ob.Nu_s_hot);
+
+  // ---- reverse
+  e = cudaMemsetAsync(ws + L.lam, 0, 2 * L.p19, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.phib, 0, 2 * L.pl, st);
+  if (e != cudaSuccess) return LTNE_ERR_CUDA;
+  C* lamL = buf19(L.lam, 0);
+  C* lamO = buf19(L.lam, 1);
+  const C inv_dT = C(1.0 / (h->p.T_hot - h->p.T_cold));
+  const int ring = 2 * (nx - 2) + 2 * (ny - 4);
+  for (int64_t s = L.nseg - 1; s >= 0 && e == cudaSuccess; --s) {
+    const int64_t a = s * K, b = (a + K < N) ? a + K : N;
+    auto slot = [&](int64_t j) { return j == 0 ? buf19(L.ckpt, s) : buf19(L.slots, j - 1); };
+    // recompute S_{a+1..b}
+    C* p0 = buf19(L.pops, 0);
+    C* p1 = buf19(L.pops, 1);
+    k_collide_pre<C><<<grd, blk, 0, st>>>(slot(0), p0, phi, P, nx, ny, pitch, plane);
+    for (int64_t j = 1; j <= b - a; ++j) {
+      k_step_record<C><<<grd, blk, 0, st>>>(p0, p1, phi, mac, P, nx, ny, pitch, plane, 0,
+                                            slot(j));
+      C* t = p0;
+      p0 = p1;
+      p1 = t;
+    }
+    if (s == L.nseg - 1)
+      k_adj_seed<C><<<(2 * ny + 255) / 256, 256, 0, st>>>(slot(b - a), lamL, phi, phib, hb, P,
+                                                          nx, ny, pitch, plane, inv_dT);
+    for (int64_t n = b - 1; n >= a; --n) {
+      if (ring > 0)
+        k_adj_wall<C><<<(ring + 127) / 128, 128, 0, st>>>(lamL, slot(n + 1 - a), phi, phib, hb,
+                                                          P, nx, ny, pitch, plane);
+      k_adj_main<C><<<grd, blk, 0, st>>>(lamL, lamO, slot(n - a), phi, phib, hb, P, nx, ny,
+                                         pitch, plane);
+      C* t = lamL;
+      lamL = lamO;
+      lamO = t;
+    }
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return LTNE_ERR_CUDA;
+  // ---- outputs
+  k_sum_plane<C><<<kSumBlocks, kRB, 0, st>>>(hb, nx, ny, pitch, part);
+  k_sum_partials<<<1, 32, 0, st>>>(part, kSumBlocks, part + kSumBlocks);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && dJ_dphi)
+    e = cudaMemcpy2DAsync(dJ_dphi, (size_t)nx * sizeof(C), phib, (size_t)pitch * sizeof(C),
+                          (size_t)nx * sizeof(C), (size_t)ny, cudaMemcpyDeviceToDevice, st);
+  double hsum = 0.0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&hsum, part + kSumBlocks, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return LTNE_ERR_CUDA;
+  // h_v/(rho c)_f = H alpha_f / L^2
+  *dJ_dH = hsum * h->alpha_f / (h->L * h->L);
+  return LTNE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ltne_adjoint_workspace_bytes(const ltne_handle* h, int64_t n_steps, int32_t segment) {
+  if (!h || n_steps < 1 || segment < 1) return 0;
+  return adj_layout(h, n_steps, segment).total;
+}
+
+int ltne_adjoint(ltne_handle* h, const double* porosity, const double* rho, const double* T_f,
+                 const double* T_s, int64_t n_steps, int32_t segment, void* adj_workspace,
+                 size_t bytes, void* dJ_dphi, double* J, double* dJ_dH) {
+  if (!h || !porosity || !J || !dJ_dH || n_steps < 1 || segment < 1 || !adj_workspace)
+    return LTNE_ERR_INVALID_ARG;
+  if (!h->ws) return LTNE_ERR_STATE;
+  const ltne_params& p = h->p;
+  if (p.bc != LTNE_BC_CAVITY || !p.porosity_field ||
+      (p.storage != LTNE_F32 && p.storage != LTNE_F64) || p.T_hot == p.T_cold)
+    return LTNE_ERR_INVALID_ARG;
+  if (bytes < ltne_adjoint_workspace_bytes(h, n_steps, segment) ||
+      (reinterpret_cast<uintptr_t>(adj_workspace) & 255u) != 0)
+    return LTNE_ERR_WORKSPACE;
+  char* ws = static_cast<char*>(adj_workspace);
+  if (p.storage == LTNE_F64)
+    return run_adjoint<double>(h, porosity, rho, T_f, T_s, n_steps, segment, ws, dJ_dphi, J,
+                               dJ_dH);
+  return run_adjoint<float>(h, porosity, rho, T_f, T_s, n_steps, segment, ws, dJ_dphi, J, dJ_dH);
+}
+
+}  // extern "C"

@@ -30,32 +30,6 @@ size_t storage_bytes(int storage) {
 
 }  // namespace
 
-struct ltne_handle {
-  ltne_params p;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  NodeParams<double> P{};
-  StepShape shape;
-  // derived lattice values
-  double L = 0, nu_f = 0, alpha_f = 0;
-  // layout
-  int64_t pitch = 0, plane = 0;
-  size_t es = 0, ec = 0;  // storage / compute element sizes
-  size_t off_pop[2] = {0, 0}, off_phi = 0, off_mac = 0, off_prev = 0, off_part = 0, off_out = 0;
-  size_t off_tick = 0;
-  size_t ws_bytes = 0;
-  char* ws = nullptr;
-  int red_blocks = 1;
-  // state
-  int cur = 0;
-  int64_t step = 0;
-  bool fields_set = false;
-  bool have_prev = false;
-  float enc_scale = 1.0f;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int64_t launches = 0;
-};
-
 namespace {
 
 int fail_cuda(cudaError_t e) {
@@ -272,7 +246,7 @@ void layout(ltne_handle* h) {
 }
 
 LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
-  LatticeArgs a;
+  LatticeArgs a{};
   a.src = h->ws + h->off_pop[src_buf];
   a.dst = h->ws + h->off_pop[src_buf ^ 1];
   a.phi = h->p.porosity_field ? h->ws + h->off_phi : nullptr;
@@ -336,6 +310,106 @@ cudaError_t build_graph(ltne_handle* h, int parity) {
 }
 
 }  // namespace
+
+namespace ltne {
+
+int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, const double* ux,
+                    const double* uy, const double* T_f, const double* T_s, void* pre_out) {
+  if (!h) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws) return LTNE_ERR_STATE;
+  const ltne_params& p = h->p;
+  if ((porosity != nullptr) != (p.porosity_field != 0)) return LTNE_ERR_INVALID_ARG;
+  const int64_t n = (int64_t)p.nx * p.ny;
+  if (porosity)
+    for (int64_t k = 0; k < n; ++k)
+      if (!in_open(porosity[k], 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
+  int rc = derive(h, porosity);
+  if (rc != LTNE_OK) return rc;
+  drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
+
+  // Stage the fields as deviations (rho - 1, ux, uy, T - T_ref; compute
+  // type) into the macro planes, then k_init.
+  const double defaults[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
+  const double refs[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
+  const double* src[5] = {rho, ux, uy, T_f, T_s};
+  std::vector<double> bd;
+  std::vector<float> bf;
+  const bool dbl = h->ec == 8;
+  if (dbl) bd.resize((size_t)n); else bf.resize((size_t)n);
+  auto stage = [&](const double* s, double dflt, double ref, char* dst) -> cudaError_t {
+    for (int64_t k = 0; k < n; ++k) {
+      const double v = (s ? s[k] : dflt) - ref;
+      if (!isfinite(v)) return cudaErrorInvalidValue;
+      if (dbl) bd[(size_t)k] = v; else bf[(size_t)k] = (float)v;
+    }
+    const void* hs = dbl ? (const void*)bd.data() : (const void*)bf.data();
+    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->ec, hs, (size_t)p.nx * h->ec,
+                                      (size_t)p.nx * h->ec, (size_t)p.ny,
+                                      cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(h->stream);  // the staging buffer is reused
+  };
+  for (int k = 0; k < 5; ++k) {
+    cudaError_t e = stage(src[k], defaults[k], refs[k],
+                          h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
+    if (e == cudaErrorInvalidValue) return LTNE_ERR_INVALID_ARG;
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  if (porosity) {
+    cudaError_t e = stage(porosity, 0.0, 0.0, h->ws + h->off_phi);
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  // Zero both population buffers (row padding included, so that state
+  // blobs are deterministic) and the residual snapshot.
+  cudaError_t e = cudaMemsetAsync(h->ws + h->off_pop[0], 0, h->off_phi - h->off_pop[0], h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->ws + h->off_prev, 0, 4 * (size_t)h->plane * h->ec, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->off_tick, 0, 2 * sizeof(uint32_t), h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  LatticeArgs a = lattice_args(h, 1, 1);  // dst = buffer 0
+  a.pre_out = pre_out;
+  switch (p.storage) {
+    case LTNE_F64: e = launch_init_f64(a, h->P, h->stream); break;
+    case LTNE_F32: e = launch_init_f32(a, h->P, h->stream); break;
+    case LTNE_F16DEV: e = launch_init_f16(a, h->P, h->stream); break;
+    default: e = launch_init_bf16(a, h->P, h->stream); break;
+  }
+  if (e != cudaSuccess) return fail_cuda(e);
+  h->cur = 0;
+  h->step = 0;
+  h->fields_set = true;
+  h->have_prev = false;
+  return LTNE_OK;
+}
+
+int reduce_handle(ltne_handle* h, double* acc) {
+  const ltne_params& p = h->p;
+  ReduceArgs a;
+  a.mac = h->ws + h->off_mac;
+  a.phi = p.porosity_field ? h->ws + h->off_phi : nullptr;
+  a.prev = h->ws + h->off_prev;
+  a.partials = reinterpret_cast<double*>(h->ws + h->off_part);
+  a.out = reinterpret_cast<double*>(h->ws + h->off_out);
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.pitch = h->pitch;
+  a.plane = h->plane;
+  a.phi_u = p.porosity;
+  a.sigma = p.sigma;
+  a.qf = p.qf;
+  a.qs = p.qs;
+  a.update_prev = 1;
+  a.blocks = h->red_blocks;
+  a.is_double = h->ec == 8;
+  cudaError_t e = launch_reduce(a, h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  e = cudaMemcpyAsync(acc, a.out, NACC * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  e = cudaStreamSynchronize(h->stream);
+  return fail_cuda(e);
+}
+
+}  // namespace ltne
 
 extern "C" {
 
@@ -404,70 +478,7 @@ int ltne_bind_workspace(ltne_handle* h, void* device_ptr, size_t bytes) {
 
 int ltne_set_fields(ltne_handle* h, const double* porosity, const double* rho, const double* ux,
                     const double* uy, const double* T_f, const double* T_s) {
-  if (!h) return LTNE_ERR_INVALID_ARG;
-  if (!h->ws) return LTNE_ERR_STATE;
-  const ltne_params& p = h->p;
-  if ((porosity != nullptr) != (p.porosity_field != 0)) return LTNE_ERR_INVALID_ARG;
-  const int64_t n = (int64_t)p.nx * p.ny;
-  if (porosity)
-    for (int64_t k = 0; k < n; ++k)
-      if (!in_open(porosity[k], 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
-  int rc = derive(h, porosity);
-  if (rc != LTNE_OK) return rc;
-  drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
-
-  // Stage the fields as deviations (rho - 1, ux, uy, T - T_ref; compute
-  // type) into the macro planes, then k_init.
-  const double defaults[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
-  const double refs[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
-  const double* src[5] = {rho, ux, uy, T_f, T_s};
-  std::vector<double> bd;
-  std::vector<float> bf;
-  const bool dbl = h->ec == 8;
-  if (dbl) bd.resize((size_t)n); else bf.resize((size_t)n);
-  auto stage = [&](const double* s, double dflt, double ref, char* dst) -> cudaError_t {
-    for (int64_t k = 0; k < n; ++k) {
-      const double v = (s ? s[k] : dflt) - ref;
-      if (!isfinite(v)) return cudaErrorInvalidValue;
-      if (dbl) bd[(size_t)k] = v; else bf[(size_t)k] = (float)v;
-    }
-    const void* hs = dbl ? (const void*)bd.data() : (const void*)bf.data();
-    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->ec, hs, (size_t)p.nx * h->ec,
-                                      (size_t)p.nx * h->ec, (size_t)p.ny,
-                                      cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(h->stream);  // the staging buffer is reused
-  };
-  for (int k = 0; k < 5; ++k) {
-    cudaError_t e = stage(src[k], defaults[k], refs[k],
-                          h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
-    if (e == cudaErrorInvalidValue) return LTNE_ERR_INVALID_ARG;
-    if (e != cudaSuccess) return fail_cuda(e);
-  }
-  if (porosity) {
-    cudaError_t e = stage(porosity, 0.0, 0.0, h->ws + h->off_phi);
-    if (e != cudaSuccess) return fail_cuda(e);
-  }
-  // Zero both population buffers (row padding included, so that state
-  // blobs are deterministic) and the residual snapshot.
-  cudaError_t e = cudaMemsetAsync(h->ws + h->off_pop[0], 0, h->off_phi - h->off_pop[0], h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(h->ws + h->off_prev, 0, 4 * (size_t)h->plane * h->ec, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->off_tick, 0, 2 * sizeof(uint32_t), h->stream);
-  if (e != cudaSuccess) return fail_cuda(e);
-  LatticeArgs a = lattice_args(h, 1, 1);  // dst = buffer 0
-  switch (p.storage) {
-    case LTNE_F64: e = launch_init_f64(a, h->P, h->stream); break;
-    case LTNE_F32: e = launch_init_f32(a, h->P, h->stream); break;
-    case LTNE_F16DEV: e = launch_init_f16(a, h->P, h->stream); break;
-    default: e = launch_init_bf16(a, h->P, h->stream); break;
-  }
-  if (e != cudaSuccess) return fail_cuda(e);
-  h->cur = 0;
-  h->step = 0;
-  h->fields_set = true;
-  h->have_prev = false;
-  return LTNE_OK;
+  return set_fields_impl(h, porosity, rho, ux, uy, T_f, T_s, nullptr);
 }
 
 int ltne_step(ltne_handle* h, int64_t n) {
@@ -506,31 +517,9 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   if (!h || !out) return LTNE_ERR_INVALID_ARG;
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;
-  ReduceArgs a;
-  a.mac = h->ws + h->off_mac;
-  a.phi = p.porosity_field ? h->ws + h->off_phi : nullptr;
-  a.prev = h->ws + h->off_prev;
-  a.partials = reinterpret_cast<double*>(h->ws + h->off_part);
-  a.out = reinterpret_cast<double*>(h->ws + h->off_out);
-  a.nx = p.nx;
-  a.ny = p.ny;
-  a.pitch = h->pitch;
-  a.plane = h->plane;
-  a.phi_u = p.porosity;
-  a.sigma = p.sigma;
-  a.qf = p.qf;
-  a.qs = p.qs;
-  a.update_prev = 1;
-  a.blocks = h->red_blocks;
-  a.is_double = h->ec == 8;
-  cudaError_t e = launch_reduce(a, h->stream);
-  if (e != cudaSuccess) return fail_cuda(e);
   double acc[NACC];
-  e = cudaMemcpyAsync(acc, a.out, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
-  if (e != cudaSuccess) return fail_cuda(e);
-  e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return fail_cuda(e);
-
+  const int rr = reduce_handle(h, acc);
+  if (rr != LTNE_OK) return rr;
   DerivedInfo info;
   info.L = h->L;
   info.nu_f = h->nu_f;

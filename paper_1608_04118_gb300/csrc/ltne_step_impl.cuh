@@ -119,7 +119,8 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
                                           const NodeParams<C>& P, const int x, const int y,
                                           const int nx, const int ny, const int64_t pitch,
                                           const int64_t plane, const C scale, const C inv_scale,
-                                          const int write_macros, const uint32_t tick) {
+                                          const int write_macros, const uint32_t tick,
+                                          C* __restrict__ pre_out = nullptr) {
   // Wall classification and the node whose neighbourhood is pulled.
   int cx = x, cy = y;
   int kind = -1;  // -1 interior, 0 hot wall, 1 cold wall, 2 adiabatic / no-slip row
@@ -161,6 +162,14 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
     if (kind == 0) dTwf = dTws = P.dT_hot;
     if (kind == 1) dTwf = dTws = P.dT_cold;
     nee<C>(P, mn, dTwf, dTws, f, gf, gs);
+  }
+  if (pre_out) {  // record the pre-collision state (reverse-mode recomputation)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) pre_out[(int64_t)i * plane + off] = f[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) pre_out[(int64_t)(9 + i) * plane + off] = gf[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) pre_out[(int64_t)(14 + i) * plane + off] = gs[i];
   }
   const Medium<C> md = phi_field ? medium_at<C>(P, phi_field[off]) : P.um;
   Macro<C> m;
@@ -209,7 +218,8 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ dst,
                                               const C* __restrict__ phi_field,
                                               C* __restrict__ mac, const NodeParams<C> P,
                                               const int nx, const int ny, const int64_t pitch,
-                                              const int64_t plane, const C scale) {
+                                              const int64_t plane, const C scale,
+                                              C* __restrict__ pre_out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -218,6 +228,14 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ dst,
   C f[9], gf[5], gs[5];
   equilibrium<C>(P, md.phi, mac[off], mac[plane + off], mac[2 * plane + off],
                  mac[3 * plane + off], mac[4 * plane + off], f, gf, gs);
+  if (pre_out) {  // S_0, for reverse-mode recomputation
+#pragma unroll
+    for (int i = 0; i < 9; ++i) pre_out[(int64_t)i * plane + off] = f[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) pre_out[(int64_t)(9 + i) * plane + off] = gf[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) pre_out[(int64_t)(14 + i) * plane + off] = gs[i];
+  }
   Macro<C> m;
   macros<C>(P, md, f, gf, gs, m);
   store_macros<C>(mac, plane, off, m);
@@ -265,7 +283,7 @@ cudaError_t launch_init_t(const LatticeArgs& a, const NodeParams<double>& Pd, cu
   dim3 grid((a.nx + 127) / 128, (a.ny + 1) / 2);
   k_init<S, C><<<grid, block, 0, st>>>(static_cast<S*>(a.dst), static_cast<const C*>(a.phi),
                                        static_cast<C*>(a.mac), P, a.nx, a.ny, a.pitch, a.plane,
-                                       C(a.enc_scale));
+                                       C(a.enc_scale), static_cast<C*>(a.pre_out));
   return cudaGetLastError();
 }
 

@@ -89,6 +89,9 @@ SIGNATURES = {
     "ltne_launch_count": (C.c_int64, [_vp]),
     "ltne_observables_static": (C.c_int, [C.POINTER(ltne_params), _vp, C.c_int64, _vp, C.c_int64,
                                           _vp, C.POINTER(ltne_obs)]),
+    "ltne_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_int64, C.c_int32]),
+    "ltne_adjoint": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.c_int64, C.c_int32, _vp, C.c_size_t, _vp,
+                               _dp, _dp]),
     "ltne_destroy": (None, [_vp]),
     "ltne_error_string": (C.c_char_p, [C.c_int]),
     "ltne_batch_create": (C.c_int, [C.POINTER(ltne_params), C.c_int32, _vp, C.POINTER(_vp)]),
@@ -219,6 +222,22 @@ def ltne_launch_count(h) -> int:
     return int(_lib().ltne_launch_count(h))
 
 
+def ltne_adjoint_workspace_bytes(h, n_steps, segment) -> int:
+    return int(_lib().ltne_adjoint_workspace_bytes(h, int(n_steps), int(segment)))
+
+
+def ltne_adjoint(h, nn, porosity, n_steps, segment, adj_ptr, adj_bytes, dJ_dphi_ptr,
+                 rho=None, T_f=None, T_s=None):
+    """Returns (J, dJ/dH); dJ/dphi is written to the device buffer."""
+    arrs = [_f64(a, nn) for a in (porosity, rho, T_f, T_s)]
+    J, dH = C.c_double(), C.c_double()
+    _check(_lib().ltne_adjoint(h, *[_ptr(a) for a in arrs], int(n_steps), int(segment),
+                               _vp(int(adj_ptr)), int(adj_bytes),
+                               _vp(int(dJ_dphi_ptr)) if dJ_dphi_ptr else None,
+                               C.byref(J), C.byref(dH)), "ltne_adjoint")
+    return J.value, dH.value
+
+
 def ltne_destroy(h):
     if h:
         _lib().ltne_destroy(h)
@@ -281,6 +300,24 @@ class Cavity:
     @property
     def launches(self):
         return ltne_launch_count(self.h)
+
+    def adjoint(self, porosity, n_steps, segment=None, rho=None, T_f=None, T_s=None):
+        """Run n_steps from the given initial fields (fluid at rest) and return
+        (J, dJ/dphi as a (ny, nx) device tensor, dJ/dH) with J = (Nu_f,hot +
+        Nu_s,hot)/2 at the last step.  segment defaults to ceil(sqrt(n))."""
+        import math
+
+        import torch
+
+        if segment is None:
+            segment = max(1, int(math.ceil(math.sqrt(n_steps))))
+        nbytes = ltne_adjoint_workspace_bytes(self.h, n_steps, segment)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.workspace.device)
+        dt = torch.float64 if self.params.storage == LTNE_F64 else torch.float32
+        g = torch.empty((self.ny, self.nx), dtype=dt, device=self.workspace.device)
+        J, dH = ltne_adjoint(self.h, self.nodes, porosity, n_steps, segment, ws.data_ptr(), nbytes,
+                             g.data_ptr(), rho=rho, T_f=T_f, T_s=T_s)
+        return J, g, dH
 
     def close(self):
         if getattr(self, "h", None):

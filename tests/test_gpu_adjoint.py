@@ -1,0 +1,161 @@
+"""Reverse-mode adjoint of the time step: gradients of
+J = (Nu_f,hot + Nu_s,hot)/2 with respect to the per-node porosity and H.
+
+Reference gradients: the oracle compiled for complex arithmetic gives
+complex-step derivatives Im J(theta + i h e_k)/h, exact to round-off
+(h = 1e-30); FP64 central differences of the forward step serve as a second
+witness at the full 256 x 256 x 4000-step size.  The Ergun particle
+diameter is held fixed in every variant (it is computed once from the
+unperturbed field).
+"""
+import numpy as np
+import pytest
+
+from paper_1608_04118_gb300 import workloads as W
+from tests.helpers import cavity_for, phys
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_04118_gb300 import build
+
+    build.build()
+
+
+SMALL = dict(nx=20, ny=16, Ra=1e5, Pr=1.0, Da=1e-3, H=50.0, gamma_sf=3.0, sigma=1.2, T_hot=1.0,
+             T_cold=0.0, T_ref=0.5, ergun=True)
+
+
+def _complex_step(cfg, phi, steps, nodes, h=1e-30):
+    from oracle import ComplexOracle, OracleParams
+
+    p = OracleParams.make(cfg["nx"], cfg["ny"], ergun_K=1, **phys(cfg))
+    out = {}
+    for k in list(nodes) + [-1]:
+        o = ComplexOracle(p, phi=phi).perturb(int(k), h).init().step(steps)
+        re, im = o.objective()
+        out[int(k)] = im / h
+        out["J"] = re
+    return out
+
+
+@pytest.fixture(scope="module")
+def small_reference():
+    phi = W.porosity_field(SMALL["nx"], SMALL["ny"], 0.4, 0.8, seed=44).reshape(-1)
+    nodes = W.fd_nodes(SMALL["nx"], SMALL["ny"], 12, seed=45)
+    ref = _complex_step(SMALL, phi, 120, nodes)
+    return phi, nodes, ref
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-9), ("f32", 1e-3)])
+def test_adjoint_matches_complex_step_oracle(small_reference, storage, tol):
+    """120 steps in segments of 16 (the last one ragged)."""
+    phi, nodes, ref = small_reference
+    cav = cavity_for(SMALL, storage=storage, phi=phi)
+    J, g, dH = cav.adjoint(phi, 120, segment=16)
+    g = g.double().cpu().numpy().reshape(-1)
+    assert J == pytest.approx(ref["J"], rel=1e-12 if storage == "f64" else 1e-5)
+    gref = np.array([ref[int(k)] for k in nodes])
+    scale = np.abs(gref).max()
+    err = np.abs(g[nodes] - gref)
+    assert err.max() <= tol * scale, (storage, err / scale)
+    assert dH == pytest.approx(ref[-1], rel=tol, abs=tol * abs(ref[-1]))
+    # the step counter and the fields are those of a plain run of 120 steps
+    ob = cav.observables()
+    assert ob["step"] == 120
+    assert 0.5 * (ob["Nu_f_hot"] + ob["Nu_s_hot"]) == pytest.approx(J, rel=1e-12)
+
+
+def test_segment_length_does_not_change_the_gradient(small_reference):
+    phi, nodes, _ = small_reference
+    outs = []
+    for seg in (1, 7, 120, 500):
+        cav = cavity_for(SMALL, storage="f64", phi=phi)
+        J, g, dH = cav.adjoint(phi, 120, segment=seg)
+        outs.append((J, g.cpu().numpy(), dH))
+    for J, g, dH in outs[1:]:
+        assert J == outs[0][0]
+        assert np.array_equal(g, outs[0][1])
+        assert dH == outs[0][2]
+
+
+def _J_fp64(cfg, phi, steps, d_p, H=None):
+    c = dict(cfg, d_p=d_p)
+    if H is not None:
+        c["H"] = H
+    cav = cavity_for(c, storage="f64", phi=phi).set_fields(porosity=phi).step(steps)
+    ob = cav.observables()
+    cav.close()
+    return 0.5 * (ob["Nu_f_hot"] + ob["Nu_s_hot"])
+
+
+def test_directional_derivative_dot_product(small_reference):
+    """<dJ/dphi, v> equals the FP64 central difference along a random v."""
+    from oracle import ergun_diameter
+
+    phi, _, _ = small_reference
+    d = ergun_diameter(phi, SMALL["ny"] - 1, SMALL["Da"])
+    cav = cavity_for(dict(SMALL, d_p=d), storage="f64", phi=phi)
+    _, g, _ = cav.adjoint(phi, 120, segment=16)
+    v = np.random.default_rng(46).standard_normal(phi.size)
+    eps = 1e-6
+    fd = (_J_fp64(SMALL, phi + eps * v, 120, d) - _J_fp64(SMALL, phi - eps * v, 120, d)) / (2 * eps)
+    assert float(g.cpu().numpy().reshape(-1) @ v) == pytest.approx(fd, rel=1e-6)
+
+
+def test_c4_fp32_adjoint_vs_fp64_central_differences():
+    """256 x 256, porosity U[0.4, 0.8] (seed 4), Ra 1e5, Da 1e-3 (Ergun, mean),
+    H 50, 4000 steps, ceil(sqrt(4000)) = 64-step segments: the FP32 adjoint
+    against FP64 central differences of the forward step on 32 interior nodes
+    (seed 40) and H."""
+    from oracle import ergun_diameter
+
+    c = W.C4_ADJOINT
+    nx, ny, steps = c["nx"], c["ny"], c["steps"]
+    cfg = {k: v for k, v in c.items() if k not in ("phi_lo", "phi_hi", "seed", "steps",
+                                                   "fd_nodes", "fd_seed")}
+    phi = W.porosity_field(nx, ny, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+    d = ergun_diameter(phi, ny - 1, c["Da"])
+    cfg["d_p"] = d
+    cav = cavity_for(cfg, storage="f32", phi=phi)
+    J, g, dH = cav.adjoint(phi, steps, segment=64)
+    g = g.double().cpu().numpy().reshape(-1)
+    nodes = W.fd_nodes(nx, ny, c["fd_nodes"], c["fd_seed"])
+    h = 1e-5
+    fd = []
+    for k in nodes:
+        pp, pm = phi.copy(), phi.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd.append((_J_fp64(cfg, pp, steps, d) - _J_fp64(cfg, pm, steps, d)) / (2 * h))
+    fd = np.array(fd)
+    hH = 1e-4 * cfg["H"]
+    fdH = (_J_fp64(cfg, phi, steps, d, H=cfg["H"] + hH)
+           - _J_fp64(cfg, phi, steps, d, H=cfg["H"] - hH)) / (2 * hH)
+    scale = np.abs(fd).max()
+    assert np.abs(g[nodes] - fd).max() <= 1e-3 * scale, np.abs(g[nodes] - fd) / scale
+    assert np.linalg.norm(g[nodes] - fd) <= 1e-3 * np.linalg.norm(fd)
+    assert dH == pytest.approx(fdH, rel=1e-3)
+    J64 = _J_fp64(cfg, phi, steps, d)
+    assert J == pytest.approx(J64, rel=1e-5)
+
+
+def test_autograd_function_returns_the_adjoint_gradient(small_reference):
+    from paper_1608_04118_gb300.autograd import wall_nusselt
+
+    phi, nodes, ref = small_reference
+    t = torch.tensor(phi.reshape(SMALL["ny"], SMALL["nx"]), dtype=torch.float64,
+                     requires_grad=True)
+    H = torch.tensor(SMALL["H"], dtype=torch.float64, requires_grad=True)
+    kw = {k: v for k, v in phys(SMALL).items() if k != "H"}
+    J = wall_nusselt(t, H, 120, 16, "f64", **kw)
+    (2.0 * J).backward()
+    gref = np.array([ref[int(k)] for k in nodes])
+    got = t.grad.numpy().reshape(-1)[nodes] / 2.0
+    assert np.abs(got - gref).max() <= 1e-9 * np.abs(gref).max()
+    assert float(H.grad) / 2.0 == pytest.approx(ref[-1], rel=1e-9)

@@ -393,3 +393,36 @@ def test_solid_diffusivity_chapman_enskog():
     a2 = amp()
     rate = -np.log(a2 / a1) / 1800
     assert rate == pytest.approx(d["alpha_s"] * k * k, rel=1e-3)
+
+
+# ---------------------------------------------------------------- p15 ----
+def test_complex_step_gradient_matches_central_differences():
+    """The complex-step variant (gradient reference of the adjoint) agrees
+    with FP64 central differences of the real oracle, for the porosity of an
+    interior node and for H, with the Ergun diameter held fixed."""
+    from oracle import ComplexOracle
+
+    nx, ny, steps = 12, 10, 60
+    phi = np.random.default_rng(47).uniform(0.4, 0.8, nx * ny)
+    kw = dict(ergun_K=1, Ra=1e5, Da=1e-3, H=50.0, gamma_sf=3.0, sigma=1.2)
+    d = Oracle(OracleParams.make(nx, ny, **kw), phi=phi).derived()["d_ergun"]
+    kw["d_p"] = d
+
+    def J(ph, H=50.0):
+        o = Oracle(OracleParams.make(nx, ny, **dict(kw, H=H)), phi=ph).init().step(steps)
+        return o.objective()[0]
+
+    pairs = []
+    for k in (3 * nx + 4, 5 * nx + 7, 2 * nx + 1):
+        co = ComplexOracle(OracleParams.make(nx, ny, **kw), phi=phi).perturb(k, 1e-30)
+        cs = co.init().step(steps).objective()[1] / 1e-30
+        h = 1e-4  # round-off of J (~1e-15) / h stays far below the tolerance
+        pp, pm = phi.copy(), phi.copy()
+        pp[k] += h
+        pm[k] -= h
+        pairs.append((cs, (J(pp) - J(pm)) / (2 * h)))
+    co = ComplexOracle(OracleParams.make(nx, ny, **kw), phi=phi).perturb(-1, 1e-30)
+    cs = co.init().step(steps).objective()[1] / 1e-30
+    pairs.append((cs, (J(phi, 50.0 + 1e-2) - J(phi, 50.0 - 1e-2)) / 2e-2))
+    cs, fd = np.array(pairs).T
+    assert np.abs(cs - fd).max() <= 1e-6 * np.abs(fd).max(), (cs, fd)
