@@ -75,6 +75,30 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, device=None):
+    """Max of a per-rank value over all ranks of the default process group
+    (the value itself when not distributed)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, t_max):
+    """Lattice updates of all ranks (independent replicas) over the slowest
+    rank's time, in millions per second."""
+    return world * nodes_per_rank * steps / t_max / 1e6
+
+
+def replica_seed(base, rank):
+    """Porosity seed of rank `rank`'s cavity (rank 0 = the single-GPU input)."""
+    return base + rank
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -446,7 +470,7 @@ def main():
 
     c = W.C2_THROUGHPUT
     n = args.n
-    phi = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], c["seed"] + rank).reshape(-1)
+    phi = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], replica_seed(c["seed"], rank)).reshape(-1)
     kw = dict(Ra=c["Ra"], Pr=c["Pr"], Da=c["Da"], H=c["H"], gamma_sf=c["gamma_sf"],
               sigma=c["sigma"], T_hot=c["T_hot"], T_cold=c["T_cold"], T_ref=c["T_ref"])
     stream = torch.cuda.Stream(dev)
@@ -478,13 +502,9 @@ def main():
     clocks = sampler.stop() if sampler else None
     t = ev0.elapsed_time(ev1) / 1e3
     launches = cav.launches - launches0
-    t_max = t
-    if ws > 1:
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t, dev)
     nodes = n * n
-    value = ws * nodes * args.steps / t_max / 1e6
+    value = whole_job_mlups(nodes, args.steps, ws, t_max)
     per_launch = t / args.steps
     peak, peak_kind = load_peaks()
     achieved = BYTES_PER_LUP[args.storage] * nodes / per_launch / 1e9
@@ -503,14 +523,10 @@ def main():
         host_ob = cav.observables()   # D2H of the observables
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        tt = te
-        if ws > 1:
-            tq = torch.tensor([te], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(tq, op=torch.distributed.ReduceOp.MAX)
-            tt = float(tq.item())
+        tt = max_over_ranks(te, dev)
         h2d = phi.nbytes + 5 * nodes * 4  # porosity + five staged fields (compute type)
-        d2h = 5 * nodes * 4 + 17 * 8
-        e2e = {"value": ws * nodes * k / tt / 1e6, "unit": UNIT,
+        d2h = 5 * nodes * 4 + 18 * 8      # five fields + the observables accumulators
+        e2e = {"value": whole_job_mlups(nodes, k, ws, tt), "unit": UNIT,
                "h2d_bytes_per_step": h2d / k, "d2h_bytes_per_step": d2h / k,
                "note": "whole run through the C ABI: set_fields from host arrays, %d steps, "
                        "get_fields + observables to host" % k}

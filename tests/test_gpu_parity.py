@@ -59,6 +59,23 @@ def test_brute_force_small(storage, shape, bc, seed):
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_internal_generation_and_constant_forchheimer(storage):
+    """Internal generation (Q_f, Q_s of Eqs. 30-31, 43-45), a constant
+    Forchheimer coefficient and the Ergun permeability with a given particle
+    diameter, from random initial fields."""
+    cfg = dict(W.random_params(12, 23, 19), qf=2e-4, qs=-1e-4, F_phi=0.068, ergun=True, d_p=0.9)
+    phi = W.porosity_field(23, 19, 0.35, 0.85, seed=13).reshape(-1)
+    fields = W.random_fields(23, 19, 112)
+    c, o = run_pair(cfg, 300, storage, phi=phi, fields=fields)
+    err = field_errors(c.fields(), o.macros())
+    for k in ("u", "Tf", "Ts"):
+        assert err[k] <= TOL[storage] * (1 if storage == "f64" else 2), (k, err)
+    if storage == "f64":
+        ob, ref = c.observables(), o.observables()
+        assert ob["energy"] == pytest.approx(ref["energy"], rel=1e-11)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_multitile_ragged_per_node_porosity(storage):
     """300 x 70 spans several 128-wide tiles with a ragged tail; per-node
     porosity with the Ergun medium (Eq. 7) and d from the mean Da."""

@@ -426,3 +426,32 @@ def test_complex_step_gradient_matches_central_differences():
     pairs.append((cs, (J(phi, 50.0 + 1e-2) - J(phi, 50.0 - 1e-2)) / 2e-2))
     cs, fd = np.array(pairs).T
     assert np.abs(cs - fd).max() <= 1e-6 * np.abs(fd).max(), (cs, fd)
+
+
+# ---------------------------------------------------------------- f3 -----
+def test_internal_generation_uniform_box():
+    """Internal generation Q''' (Eqs. 30-31, 43-45) in a uniform periodic box:
+    the weighted temperature phi T_f + (1-phi) sigma T_s grows by exactly
+    phi Q_f + (1-phi) sigma Q_s per step (the exchange terms cancel), and
+    the phase difference follows the trapezoid recurrence
+    D^{n+1} (1 + k/2) = D^n (1 - k/2) + (Q_f - Q_s), k = a + b."""
+    nx = ny = 4
+    phi, sigma, qf, qs = 0.55, 1.7, 3e-4, -1e-4
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=1e4, H=300.0, porosity=phi,
+                                 sigma=sigma, gamma_sf=2.0, qf=qf, qs=qs))
+    o.init(Tf=np.full(nx * ny, 0.7), Ts=np.full(nx * ny, 0.2))
+    _, _, _, m, _, _ = o.node(0, *[x[0, 0] for x in o.get_pops()])
+    k = m["a"] + m["b"]
+    mac = o.macros()
+    W0 = phi * mac["Tf"][0, 0] + (1 - phi) * sigma * mac["Ts"][0, 0]
+    D = mac["Tf"][0, 0] - mac["Ts"][0, 0]
+    for n in range(1, 30):
+        o.step(1)
+        mac = o.macros()
+        W = phi * mac["Tf"] + (1 - phi) * sigma * mac["Ts"]
+        assert np.allclose(W, W0 + n * (phi * qf + (1 - phi) * sigma * qs), rtol=1e-13, atol=1e-15)
+        D = (D * (1 - k / 2) + (qf - qs)) / (1 + k / 2)
+        assert np.allclose(mac["Tf"] - mac["Ts"], D, rtol=1e-12, atol=1e-15)
+    o.step(5000)
+    mac = o.macros()
+    assert np.allclose(mac["Tf"] - mac["Ts"], (qf - qs) / k, rtol=1e-9)
