@@ -68,7 +68,7 @@ LTNE_HD void medium_adjoint(const NodeParams<C>& P, C phi, const MediumBar<C>& m
     if (P.fmode == 1) {
       dc1 = -P.erg_b * ip4 * (phi + C(3) * om);
     } else {
-      dc1 = -P.erg_c * ip * ip / csqrt_<C>(phi) * (phi + C(1.5) * om);
+      dc1 = -P.erg_c * ip * ip * rcp_<C>(sqrt_<C>(phi)) * (phi + C(1.5) * om);
     }
   }
   pb += c0_b * dc0 + c1_b * dc1;
@@ -96,12 +96,12 @@ LTNE_HD void macros_adjoint(const NodeParams<C>& P, const Medium<C>& md, const C
   const C rho = P.rho0 + drho;
   const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const C jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-  const C ir = C(1) / rho;
+  const C ir = rcp_<C>(rho);
   const C vx = jx * ir + C(0.5) * phi * Gx;
   const C vy = jy * ir + C(0.5) * phi * Gy;
-  const C vmag = csqrt_<C>(vx * vx + vy * vy);
-  const C R = csqrt_<C>(md.l0 * md.l0 + md.l1 * vmag);
-  const C id = C(1) / (md.l0 + R);
+  const C vmag = sqrt_<C>(vx * vx + vy * vy);
+  const C R = sqrt_<C>(md.l0 * md.l0 + md.l1 * vmag);
+  const C id = rcp_<C>(md.l0 + R);
   const C ux = vx * id, uy = vy * id, umag = vmag * id;
   const C drag = md.c0 + md.c1 * umag;
 

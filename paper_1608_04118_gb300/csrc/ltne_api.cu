@@ -150,7 +150,13 @@ int derive_params(const ltne_params& p, const double* porosity, NodeParams<doubl
 
 int validate_params(const ltne_params& p) {
   if (p.nx < 4 || p.ny < 4) return LTNE_ERR_INVALID_ARG;
-  if ((int64_t)p.nx * p.ny > (int64_t)1 << 31) return LTNE_ERR_INVALID_ARG;
+  // 19 padded planes must stay below 2^32 elements (32-bit element indices
+  // in the kernels): at most about 2.2e8 nodes, e.g. 14800 x 14800.
+  {
+    const int64_t pitch = ((int64_t)p.nx + 63) / 64 * 64;
+    const int64_t plane = (pitch * p.ny + 127) / 128 * 128;
+    if (19 * plane >= ((int64_t)1 << 32)) return LTNE_ERR_INVALID_ARG;
+  }
   if (p.storage < LTNE_F64 || p.storage > LTNE_BF16DEV) return LTNE_ERR_INVALID_ARG;
   if (p.bc < LTNE_BC_CAVITY || p.bc > LTNE_BC_CHANNEL) return LTNE_ERR_INVALID_ARG;
   if (p.permeability != LTNE_K_DARCY && p.permeability != LTNE_K_ERGUN) return LTNE_ERR_INVALID_ARG;

@@ -97,6 +97,30 @@ LTNE_HD C div_small(C x, C d, C rc) {
   return cfma_<C>(r, rc, q);
 }
 
+// Reciprocal and square root of non-conserved quantities (porosity-derived
+// coefficients, 1/rho and the velocity solve of Eq. 20).  FP32 uses the
+// hardware approximations (about 1 ulp, no long IEEE expansion; errors in
+// these quantities relax each step instead of accumulating); FP64 keeps the
+// correctly rounded operations.
+template <typename C> LTNE_HD C rcp_(C x);
+template <> LTNE_HD double rcp_<double>(double x) { return 1.0 / x; }
+template <> LTNE_HD float rcp_<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(1.0f, x);
+#else
+  return 1.0f / x;
+#endif
+}
+template <typename C> LTNE_HD C sqrt_(C x);
+template <> LTNE_HD double sqrt_<double>(double x) { return sqrt(x); }
+template <> LTNE_HD float sqrt_<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#else
+  return sqrtf(x);
+#endif
+}
+
 template <typename C> LTNE_HD C csqrt_(C x);
 template <> LTNE_HD float csqrt_<float>(float x) { return sqrtf(x); }
 template <> LTNE_HD double csqrt_<double>(double x) { return sqrt(x); }
@@ -110,16 +134,16 @@ template <typename C>
 LTNE_HD Medium<C> medium_at(const NodeParams<C>& P, C phi) {
   Medium<C> md;
   md.phi = phi;
-  md.inv_phi = C(1) / phi;
+  md.inv_phi = rcp_<C>(phi);
   md.a = P.hcoef * md.inv_phi;
-  md.b = P.hcoef / ((C(1) - phi) * P.sigma);
-  md.inv_1d = C(1) / (C(1) + C(0.5) * md.a + C(0.5) * md.b);
+  md.b = P.hcoef * rcp_<C>((C(1) - phi) * P.sigma);
+  md.inv_1d = rcp_<C>(C(1) + C(0.5) * md.a + C(0.5) * md.b);
   if (P.kmode == 0) {
     md.c0 = P.nu_over_K;
     if (P.fmode == 0) {
       md.c1 = P.Fconst * P.inv_sqrtK;
     } else {
-      md.c1 = C(1.75) / csqrt_<C>(C(150) * phi * phi * phi) * P.inv_sqrtK;
+      md.c1 = C(1.75) * rcp_<C>(sqrt_<C>(C(150) * phi * phi * phi)) * P.inv_sqrtK;
     }
   } else {
     const C om = C(1) - phi;
@@ -128,7 +152,7 @@ LTNE_HD Medium<C> medium_at(const NodeParams<C>& P, C phi) {
     if (P.fmode == 1) {
       md.c1 = P.erg_b * om * ip3;
     } else {
-      md.c1 = P.erg_c * om * md.inv_phi / csqrt_<C>(phi);
+      md.c1 = P.erg_c * om * md.inv_phi * rcp_<C>(sqrt_<C>(phi));
     }
   }
   md.l0 = C(0.5) * (C(1) + C(0.5) * phi * md.c0);  // Eq. 22
@@ -167,11 +191,11 @@ LTNE_HD void macros(const NodeParams<C>& P, const Medium<C>& md,
   m.rho = P.rho0 + m.drho;
   m.jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   m.jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-  const C inv_rho = C(1) / m.rho;
+  const C inv_rho = rcp_<C>(m.rho);
   const C vx = m.jx * inv_rho + C(0.5) * phi * Gx;  // Eq. 21
   const C vy = m.jy * inv_rho + C(0.5) * phi * Gy;
-  const C vmag = csqrt_<C>(vx * vx + vy * vy);
-  const C inv_den = C(1) / (md.l0 + csqrt_<C>(md.l0 * md.l0 + md.l1 * vmag));  // Eq. 20
+  const C vmag = sqrt_<C>(vx * vx + vy * vy);
+  const C inv_den = rcp_<C>(md.l0 + sqrt_<C>(md.l0 * md.l0 + md.l1 * vmag));  // Eq. 20
   m.ux = vx * inv_den;
   m.uy = vy * inv_den;
   m.umag = vmag * inv_den;

@@ -53,28 +53,33 @@ struct Pops {
                                               int64_t plane, int x, int xm, int xp, int y,
                                               int ym, int yp, C inv_scale, C (&f)[9],
                                               C (&gf)[5], C (&gs)[5]) {
-    const int64_t r0 = (int64_t)y * pitch, rm = (int64_t)ym * pitch, rp = (int64_t)yp * pitch;
+    // Element indices are 32-bit: 19 planes of a lattice stay below 2^32
+    // elements (checked at create), so each access is one 32-bit add and one
+    // wide multiply-add into the address.
+    const uint32_t pl = (uint32_t)plane, pi = (uint32_t)pitch;
+    const uint32_t r0 = (uint32_t)y * pi, rm = (uint32_t)ym * pi, rp = (uint32_t)yp * pi;
+    const uint32_t ux = (uint32_t)x, uxm = (uint32_t)xm, uxp = (uint32_t)xp;
     // D2Q9 e_i (Eq. 8): 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1)
     //                   5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
-    const int64_t src_off[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x,
-                                rm + xm, rm + xp, rp + xp, rp + xm};
+    const uint32_t so[9] = {r0 + ux, r0 + uxm, rm + ux, r0 + uxp, rp + ux,
+                            rm + uxm, rm + uxp, rp + uxp, rp + uxm};
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      f[i] = Codec<S, C>::dec(src[(int64_t)i * plane + src_off[i]], inv_scale);
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-      gf[i] = Codec<S, C>::dec(src[(int64_t)(9 + i) * plane + src_off[i]], inv_scale);
+    for (int i = 0; i < 9; ++i) f[i] = Codec<S, C>::dec(src[(uint32_t)i * pl + so[i]], inv_scale);
 #pragma unroll
     for (int i = 0; i < 5; ++i)
-      gs[i] = Codec<S, C>::dec(src[(int64_t)(14 + i) * plane + src_off[i]], inv_scale);
+      gf[i] = Codec<S, C>::dec(src[(uint32_t)(9 + i) * pl + so[i]], inv_scale);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      gs[i] = Codec<S, C>::dec(src[(uint32_t)(14 + i) * pl + so[i]], inv_scale);
   }
 
   // Writes the 19 post-collision deviations of the node at offset off.
   // seed_node / seed_step key the stochastic rounding of the 16-bit forms.
-  static __device__ __forceinline__ void store(S* __restrict__ dst, int64_t plane, int64_t off,
+  static __device__ __forceinline__ void store(S* __restrict__ dst, int64_t plane, uint32_t off,
                                                C scale, const C (&f)[9], const C (&gf)[5],
                                                const C (&gs)[5], uint32_t seed_node,
                                                uint32_t seed_step) {
+    const uint32_t pl = (uint32_t)plane;
     if constexpr (Codec<S, C>::kStochastic) {
       RandomBits rb(seed_node, seed_step);
       uint32_t r = 0;
@@ -83,32 +88,30 @@ struct Pops {
         if ((i & 1) == 0) r = rb.next();
         const uint32_t ri = (i & 1) ? (r >> 16) : r;
         const C v = i < 9 ? f[i] : (i < 14 ? gf[i - 9] : gs[i - 14]);
-        dst[(int64_t)i * plane + off] = Codec<S, C>::enc(v, scale, ri);
+        dst[(uint32_t)i * pl + off] = Codec<S, C>::enc(v, scale, ri);
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) dst[(int64_t)i * plane + off] = Codec<S, C>::enc(f[i], scale, 0);
+      for (int i = 0; i < 9; ++i) dst[(uint32_t)i * pl + off] = Codec<S, C>::enc(f[i], scale, 0);
 #pragma unroll
       for (int i = 0; i < 5; ++i)
-        dst[(int64_t)(9 + i) * plane + off] = Codec<S, C>::enc(gf[i], scale, 0);
+        dst[(uint32_t)(9 + i) * pl + off] = Codec<S, C>::enc(gf[i], scale, 0);
 #pragma unroll
       for (int i = 0; i < 5; ++i)
-        dst[(int64_t)(14 + i) * plane + off] = Codec<S, C>::enc(gs[i], scale, 0);
+        dst[(uint32_t)(14 + i) * pl + off] = Codec<S, C>::enc(gs[i], scale, 0);
     }
   }
 };
 
-// The macro planes hold deviations (rho - rho0, ux, uy, T_f - T0, T_s - T0)
-// so that FP32 keeps its full relative precision on them; the host adds the
-// references back in FP64.
 template <typename C>
-__device__ __forceinline__ void store_macros(C* __restrict__ mac, int64_t plane, int64_t off,
+__device__ __forceinline__ void store_macros(C* __restrict__ mac, int64_t plane, uint32_t off,
                                              const Macro<C>& m) {
+  const uint32_t pl = (uint32_t)plane;
   mac[off] = m.drho;
-  mac[plane + off] = m.ux;
-  mac[2 * plane + off] = m.uy;
-  mac[3 * plane + off] = m.dTf;
-  mac[4 * plane + off] = m.dTs;
+  mac[pl + off] = m.ux;
+  mac[2 * pl + off] = m.uy;
+  mac[3 * pl + off] = m.dTf;
+  mac[4 * pl + off] = m.dTs;
 }
 
 // One node (x, y) of one time step: pull, wall rebuild, macroscopic values,
@@ -153,9 +156,10 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
   C f[9], gf[5], gs[5];
   Pops<S, C>::pull(src, pitch, plane, cx, xm, xp, cy, ym, yp, inv_scale, f, gf, gs);
 
-  const int64_t off = (int64_t)y * pitch + x;
+  const uint32_t off = (uint32_t)y * (uint32_t)pitch + (uint32_t)x;
   if (BC != BC_PERIODIC && kind >= 0) {
-    const Medium<C> mdn = phi_field ? medium_at<C>(P, phi_field[(int64_t)cy * pitch + cx]) : P.um;
+    const Medium<C> mdn =
+        phi_field ? medium_at<C>(P, phi_field[(uint32_t)cy * (uint32_t)pitch + (uint32_t)cx]) : P.um;
     Macro<C> mn;
     macros<C>(P, mdn, f, gf, gs, mn);
     C dTwf = mn.dTf, dTws = mn.dTs;  // adiabatic: the neighbour's temperature
