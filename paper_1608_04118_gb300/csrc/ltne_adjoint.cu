@@ -259,6 +259,61 @@ __global__ void k_sum_partials(const double* __restrict__ part, int n, double* _
   }
 }
 
+template <typename C>
+__global__ void __launch_bounds__(256) k_copy19(const C* __restrict__ src, C* __restrict__ dst,
+                                                int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src[k];
+}
+
+// A captured launch sequence whose first kernel's arguments are replaced
+// before each replay (the only argument that changes between segments).
+struct SegGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t root = nullptr;
+  ~SegGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  template <typename F>
+  cudaError_t capture(cudaStream_t cap, F&& body) {
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t le = body(cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return le != cudaSuccess ? le : e;
+    }
+    size_t nroot = 1;
+    e = cudaGraphGetRootNodes(g, &root, &nroot);
+    if (e == cudaSuccess && nroot != 1) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return e;
+    }
+    graph = g;
+    return cudaSuccess;
+  }
+  // Replace the root kernel's arguments and launch.
+  cudaError_t launch(void* func, dim3 grid, dim3 block, void** args, cudaStream_t st) {
+    cudaKernelNodeParams kp = {};
+    kp.func = func;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(exec, root, &kp);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    return e;
+  }
+};
+
 constexpr int kSumBlocks = 128;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -266,7 +321,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct AdjLayout {
   int64_t nseg = 0;
   size_t p19 = 0, pl = 0;  // bytes of 19 planes, of one plane
-  size_t ckpt = 0, slots = 0, pops = 0, lam = 0, phib = 0, hb = 0, part = 0, total = 0;
+  size_t ckpt = 0, slots = 0, seg0 = 0, pops = 0, lam = 0, phib = 0, hb = 0, part = 0, total = 0;
 };
 
 AdjLayout adj_layout(const ltne_handle* h, int64_t n_steps, int32_t segment) {
@@ -280,6 +335,8 @@ AdjLayout adj_layout(const ltne_handle* h, int64_t n_steps, int32_t segment) {
   off += (size_t)L.nseg * L.p19;
   L.slots = off;
   off += (size_t)segment * L.p19;
+  L.seg0 = off;  // copy of the segment's checkpoint for graph replay
+  off += L.p19;
   L.pops = off;
   off += 2 * L.p19;
   L.lam = off;
@@ -318,18 +375,60 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
   const dim3 blk(128, 2), grd((nx + 127) / 128, (ny + 1) / 2);
   cudaError_t e = cudaSuccess;
 
-  // ---- forward, recording S at the start of every segment
-  for (int64_t n = 0; n < N && e == cudaSuccess; ++n) {
+  // ---- forward, recording S at the start of every segment.  Step n
+  // produces S_{n+1}; it records when n + 1 is a multiple of K.  Runs of K
+  // steps whose first step records (and whose last is not the final step)
+  // replay a captured graph with the checkpoint pointer replaced.
+  if (!h->cap_stream) {
+    e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return LTNE_ERR_CUDA;
+  }
+  auto fwd_step = [&](cudaStream_t s_, int src_buf, int wm, C* rec) {
+    const C* src = reinterpret_cast<const C*>(h->ws + h->off_pop[src_buf]);
+    C* dst = reinterpret_cast<C*>(h->ws + h->off_pop[src_buf ^ 1]);
+    k_step_record<C><<<grd, blk, 0, s_>>>(src, dst, phi, mac, P, nx, ny, pitch, plane, wm, rec);
+    return cudaGetLastError();
+  };
+  SegGraph gf[2];
+  int64_t n = 0;
+  while (n < N && e == cudaSuccess) {
     const int64_t a = n + 1;
-    C* rec = (a % K == 0 && a < N) ? buf19(L.ckpt, a / K) : nullptr;
-    const C* src = reinterpret_cast<const C*>(h->ws + h->off_pop[h->cur]);
-    C* dst = reinterpret_cast<C*>(h->ws + h->off_pop[h->cur ^ 1]);
-    k_step_record<C><<<grd, blk, 0, st>>>(src, dst, phi, mac, P, nx, ny, pitch, plane,
-                                          n == N - 1 ? 1 : 0, rec);
-    e = cudaGetLastError();
-    h->cur ^= 1;
-    ++h->step;
-    ++h->launches;
+    const bool records = (a % K == 0) && a < N;
+    if (records && K > 1 && n + K < N) {
+      const int par = h->cur;
+      if (!gf[par].exec)
+        e = gf[par].capture(h->cap_stream, [&](cudaStream_t cs) {
+          int b = par;
+          cudaError_t le = cudaSuccess;
+          for (int j = 0; j < K && le == cudaSuccess; ++j) {
+            le = fwd_step(cs, b, 0, j == 0 ? buf19(L.ckpt, 1) : nullptr);
+            b ^= 1;
+          }
+          return le;
+        });
+      if (e != cudaSuccess) break;
+      const C* src = reinterpret_cast<const C*>(h->ws + h->off_pop[par]);
+      C* dst = reinterpret_cast<C*>(h->ws + h->off_pop[par ^ 1]);
+      C* rec = buf19(L.ckpt, a / K);
+      int wm = 0;
+      int inx = nx, iny = ny;
+      int64_t ipitch = pitch, iplane = plane;
+      NodeParams<C> iP = P;
+      const C* iphi = phi;
+      C* imac = mac;
+      void* args[] = {&src, &dst, &iphi, &imac, &iP, &inx, &iny, &ipitch, &iplane, &wm, &rec};
+      e = gf[par].launch(reinterpret_cast<void*>(k_step_record<C>), grd, blk, args, st);
+      if (K & 1) h->cur ^= 1;
+      h->step += K;
+      h->launches += K;
+      n += K;
+    } else {
+      e = fwd_step(st, h->cur, n == N - 1 ? 1 : 0, records ? buf19(L.ckpt, a / K) : nullptr);
+      h->cur ^= 1;
+      ++h->step;
+      ++h->launches;
+      ++n;
+    }
   }
   if (e != cudaSuccess) return LTNE_ERR_CUDA;
   double acc[NACC];
@@ -352,34 +451,66 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
   C* lamO = buf19(L.lam, 1);
   const C inv_dT = C(1.0 / (h->p.T_hot - h->p.T_cold));
   const int ring = 2 * (nx - 2) + 2 * (ny - 4);
-  for (int64_t s = L.nseg - 1; s >= 0 && e == cudaSuccess; --s) {
-    const int64_t a = s * K, b = (a + K < N) ? a + K : N;
-    auto slot = [&](int64_t j) { return j == 0 ? buf19(L.ckpt, s) : buf19(L.slots, j - 1); };
-    // recompute S_{a+1..b}
+  const int64_t n19 = 19 * plane;
+  // One segment's recompute and reverse sweep; slot 0 is S_a.
+  auto segment_body = [&](cudaStream_t s_, int64_t len, C* slot0, bool seed, C*& lL, C*& lO) {
+    auto slot = [&](int64_t j) { return j == 0 ? slot0 : buf19(L.slots, j - 1); };
     C* p0 = buf19(L.pops, 0);
     C* p1 = buf19(L.pops, 1);
-    k_collide_pre<C><<<grd, blk, 0, st>>>(slot(0), p0, phi, P, nx, ny, pitch, plane);
-    for (int64_t j = 1; j <= b - a; ++j) {
-      k_step_record<C><<<grd, blk, 0, st>>>(p0, p1, phi, mac, P, nx, ny, pitch, plane, 0,
+    k_collide_pre<C><<<grd, blk, 0, s_>>>(slot(0), p0, phi, P, nx, ny, pitch, plane);
+    for (int64_t j = 1; j <= len; ++j) {
+      k_step_record<C><<<grd, blk, 0, s_>>>(p0, p1, phi, mac, P, nx, ny, pitch, plane, 0,
                                             slot(j));
       C* t = p0;
       p0 = p1;
       p1 = t;
     }
-    if (s == L.nseg - 1)
-      k_adj_seed<C><<<(2 * ny + 255) / 256, 256, 0, st>>>(slot(b - a), lamL, phi, phib, hb, P,
-                                                          nx, ny, pitch, plane, inv_dT);
-    for (int64_t n = b - 1; n >= a; --n) {
+    if (seed)
+      k_adj_seed<C><<<(2 * ny + 255) / 256, 256, 0, s_>>>(slot(len), lL, phi, phib, hb, P, nx,
+                                                          ny, pitch, plane, inv_dT);
+    for (int64_t j = len - 1; j >= 0; --j) {
       if (ring > 0)
-        k_adj_wall<C><<<(ring + 127) / 128, 128, 0, st>>>(lamL, slot(n + 1 - a), phi, phib, hb,
-                                                          P, nx, ny, pitch, plane);
-      k_adj_main<C><<<grd, blk, 0, st>>>(lamL, lamO, slot(n - a), phi, phib, hb, P, nx, ny,
-                                         pitch, plane);
-      C* t = lamL;
-      lamL = lamO;
-      lamO = t;
+        k_adj_wall<C><<<(ring + 127) / 128, 128, 0, s_>>>(lL, slot(j + 1), phi, phib, hb, P, nx,
+                                                          ny, pitch, plane);
+      k_adj_main<C><<<grd, blk, 0, s_>>>(lL, lO, slot(j), phi, phib, hb, P, nx, ny, pitch,
+                                         plane);
+      C* t = lL;
+      lL = lO;
+      lO = t;
     }
-    e = cudaGetLastError();
+    return cudaGetLastError();
+  };
+  // Full segments other than the last replay one graph (per adjoint-buffer
+  // parity) whose root copies the segment's checkpoint into slot 0.
+  SegGraph gr[2];
+  C* seg0 = buf19(L.seg0, 0);
+  const dim3 cgrid(1216), cblk(256);
+  for (int64_t s = L.nseg - 1; s >= 0 && e == cudaSuccess; --s) {
+    const int64_t a = s * K, b = (a + K < N) ? a + K : N;
+    const bool last = (s == L.nseg - 1);
+    if (!last && b - a == K && K > 1) {
+      const int par = (lamL == buf19(L.lam, 0)) ? 0 : 1;
+      if (!gr[par].exec)
+        e = gr[par].capture(h->cap_stream, [&](cudaStream_t cs) {
+          k_copy19<C><<<cgrid, cblk, 0, cs>>>(buf19(L.ckpt, 0), seg0, n19);
+          C* lL = buf19(L.lam, par);
+          C* lO = buf19(L.lam, par ^ 1);
+          return segment_body(cs, K, seg0, false, lL, lO);
+        });
+      if (e != cudaSuccess) break;
+      const C* src = buf19(L.ckpt, s);
+      C* dst = seg0;
+      int64_t cnt = n19;
+      void* args[] = {&src, &dst, &cnt};
+      e = gr[par].launch(reinterpret_cast<void*>(k_copy19<C>), cgrid, cblk, args, st);
+      if (K & 1) {
+        C* t = lamL;
+        lamL = lamO;
+        lamO = t;
+      }
+    } else {
+      e = segment_body(st, b - a, buf19(L.ckpt, s), last, lamL, lamO);
+    }
   }
   if (e != cudaSuccess) return LTNE_ERR_CUDA;
   // ---- outputs
