@@ -103,6 +103,20 @@ typedef struct ltne_params {
   double varpi;            /* thermal weight parameter (Sec. 3.2), (0, 1)    */
   double ext_ax, ext_ay;   /* extra body acceleration added to G (tests)     */
   double nu_override;      /* > 0: nu_f in lattice units (needed for Ra = 0) */
+  int32_t hv_local;        /* 1: h_v per node from the correlation of Eq. 52,
+                              H_p = h_v D_p^2 / k_f = 0.376 Re^0.644 Pr^0.37,
+                              Re = u_m D_p / nu_f, with u_m the node's |u| in
+                              the previous state (the initial field's |u| for
+                              the initial state; the paper leaves u_m and its
+                              time level open); H is then unused.  Not
+                              supported by the batched form or the adjoint. */
+  int32_t thermal_correction; /* 1: add the correction term of Sec. 3.2,
+                              dt N^-1 (I - Q/2) C with C = N C~ and
+                              C~_i = w~_i T_f (e_i.F) / (phi c_sT^2), to the
+                              fluid-phase equation (Eq. 27); the paper
+                              neglects it (0, default).  Not supported by the
+                              batched form. */
+  double Dp_over_L;        /* D_p / L of Eq. 52 (Sec. 4: 0.0135)            */
 } ltne_params;
 
 /* Observables of the current state, reduced on the device in FP64.
@@ -173,8 +187,11 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
                     double* T_s);
 
 /* Checkpoint: size of the state blob, and copies of it to / from host
-   memory.  A restored handle continues bit for bit as if it had never
-   stopped.  Synchronises the stream. */
+   memory.  The blob holds the populations, the macroscopic fields, the
+   per-node porosity (if any), the previous |u| of the local h_v model (if
+   on), the step and the Ergun diameter in use, so a handle created with the
+   same parameters and restored from it continues bit for bit as if it had
+   never stopped.  Synchronises the stream. */
 size_t ltne_state_bytes(const ltne_handle* h);
 int ltne_get_state(ltne_handle* h, void* host, size_t bytes);
 int ltne_set_state(ltne_handle* h, const void* host, size_t bytes);

@@ -44,6 +44,12 @@
  *       columns and use the diagonal neighbour; on adiabatic rows the wall
  *       temperature is the neighbour's, phase by phase; u_wall = 0.
  *   R5  H is the constant H_v = h_v L^2 / k_f, so h_v/(rho c)_f = H alpha_f/L^2.
+ *   R6  with the local correlation of Eq. 52 (hv_local), h_v/(rho c)_f =
+ *       H_p alpha_f / D_p^2 with H_p = 0.376 Re^0.644 Pr^0.37 and
+ *       Re = u_m D_p / nu_f, D_p = 0.0135 L; u_m, left undefined by the
+ *       paper, is the node's |u| in the previous state (the initial field's
+ *       |u| for S_0), so the temperature solve that precedes the velocity
+ *       solve of a step stays explicit.
  */
 #include <math.h>
 #include <complex.h>
@@ -82,6 +88,9 @@ typedef struct orc_params {
   double T_hot, T_cold, T_ref, Ma, F_phi, d_p, qf, qs;
   double s_e, s_eps, s_q, zeta_e, zeta_nu, eta_e, eta_nu, varpi;
   double ext_ax, ext_ay, nu_override;
+  int32_t hv_local;     /* 1: h_v per node from Eq. 52 (reading R6 below)    */
+  int32_t thermal_correction; /* 1: add the correction term of Sec. 3.2       */
+  double Dp_over_L;     /* D_p / L of Eq. 52                                */
   double L_ref;         /* > 0: characteristic length L (else ny - 1); lets a
                            window of a larger cavity use that cavity's L  */
 } orc_params;
@@ -103,6 +112,8 @@ typedef struct orc_state {
   double wt[5];               /* thermal weights w~ (Sec. 3.2)                  */
   real_t H;
   real_t *phi, *K, *Fphi;     /* per node */
+  real_t *hv;                 /* per node h_v / (rho c)_f                       */
+  double *um, *um_next;       /* per node |u| of the previous state (Eq. 52)    */
   real_t *f, *gf, *gs;
   real_t *fn, *gfn, *gsn;
   long step;
@@ -258,10 +269,20 @@ typedef struct node_macro {
   real_t rho, ux, uy, Tf, Ts, Gx, Gy, Fx, Fy, a, b;
 } node_macro;
 
-/* Interphase coefficients of Eq. 42 with reading R5:
-   a = h_v/(phi (rho c)_f),  b = h_v/((1-phi)(rho c)_s). */
-static void exchange_coeffs(const orc_state* st, real_t phi, real_t* a, real_t* b) {
-  real_t hv_f = st->H * st->alpha_f / (st->L * st->L); /* h_v / (rho c)_f */
+/* h_v / (rho c)_f at a node whose previous |u| is um (readings R5, R6). */
+static real_t hv_of(const orc_state* st, double um) {
+  const orc_params* p = &st->p;
+  if (!p->hv_local) return st->H * st->alpha_f / (st->L * st->L);
+  double Dp = p->Dp_over_L * st->L;
+  double Re = um * Dp / st->nu_f;                               /* Eq. 52 */
+  double Hp = 0.376 * pow(Re, 0.644) * pow(p->Pr, 0.37);
+  return Hp * st->alpha_f / (Dp * Dp);
+}
+
+/* Interphase coefficients of Eq. 42: a = h_v/(phi (rho c)_f),
+   b = h_v/((1-phi)(rho c)_s), with the node's h_v. */
+static void exchange_coeffs(const orc_state* st, int n, real_t phi, real_t* a, real_t* b) {
+  real_t hv_f = st->hv[n]; /* h_v / (rho c)_f */
   *a = hv_f / phi;
   *b = hv_f / ((1 - phi) * st->p.sigma);
 }
@@ -275,7 +296,7 @@ static void node_macros(const orc_state* st, int n, const real_t* f, const real_
   const orc_params* p = &st->p;
   const orc_lattice* lat = &st->lat;
   real_t phi = st->phi[n], K = st->K[n], Fphi = st->Fphi[n];
-  exchange_coeffs(st, phi, &m->a, &m->b);
+  exchange_coeffs(st, n, phi, &m->a, &m->b);
   real_t d0 = 0.5 * m->a, d1 = 0.5 * m->b; /* Eq. 46, dt = 1 */
   real_t sum_gf = 0, sum_gs = 0;
   for (int i = 0; i < 5; ++i) {
@@ -416,6 +437,15 @@ static void node_collide(const orc_state* st, int n, const real_t* f, const real
   nfeq[4] = 0;
   for (int k = 0; k < 5; ++k)
     nfs[k] = nf[k] - st->Qf[k] * (nf[k] - nfeq[k]) + (1 - 0.5 * st->Qf[k]) * psi_f[k];
+  if (p->thermal_correction) {
+    /* Correction term of Sec. 3.2: dt (I - Q/2) C, C = N C~,
+       C~_i = w~_i T_f (e_i.F) / (phi c_sT^2). */
+    real_t Ct[5], Cm[5];
+    for (int i = 0; i < 5; ++i)
+      Ct[i] = st->wt[i] * m.Tf * (lat->ex[i] * m.Fx + lat->ey[i] * m.Fy) / (phi * st->csT2);
+    matvec5(lat->N, Ct, Cm);
+    for (int k = 0; k < 5; ++k) nfs[k] += (1 - 0.5 * st->Qf[k]) * Cm[k];
+  }
   matvec5(lat->Ninv, nfs, gfo);
   /* Solid phase: Eq. 38 equilibrium moments, Eq. 33 collision. */
   real_t ns[5], nseq[5], nss[5];
@@ -521,6 +551,9 @@ orc_state* ORC(create)(const orc_params* p, const double* phi) {
   st->fn = calloc((size_t)st->nn * 9, sizeof(real_t));
   st->gfn = calloc((size_t)st->nn * 5, sizeof(real_t));
   st->gsn = calloc((size_t)st->nn * 5, sizeof(real_t));
+  st->hv = calloc((size_t)st->nn, sizeof(real_t));
+  st->um = calloc((size_t)st->nn, sizeof(double));
+  st->um_next = calloc((size_t)st->nn, sizeof(double));
   derive(st, phi);
   for (int n = 0; n < st->nn; ++n) node_medium(st, n);
   return st;
@@ -531,6 +564,7 @@ void ORC(destroy)(orc_state* st) {
   free(st->phi); free(st->K); free(st->Fphi);
   free(st->f); free(st->gf); free(st->gs);
   free(st->fn); free(st->gfn); free(st->gsn);
+  free(st->hv); free(st->um); free(st->um_next);
   free(st);
 }
 
@@ -541,6 +575,8 @@ void ORC(init)(orc_state* st, const double* rho, const double* ux, const double*
   for (int n = 0; n < st->nn; ++n) {
     real_t r = rho ? rho[n] : 1.0, vx = ux ? ux[n] : 0.0, vy = uy ? uy[n] : 0.0;
     real_t tf = Tf ? Tf[n] : st->p.T_ref, ts = Ts ? Ts[n] : st->p.T_ref;
+    st->um[n] = sqrt(RE(vx) * RE(vx) + RE(vy) * RE(vy));
+    st->hv[n] = hv_of(st, st->um[n]);
     feq(st, r, vx, vy, st->phi[n], st->f + 9 * n);
     gfeq(st, tf, vx, vy, st->phi[n], st->gf + 5 * n);
     gseq(st, ts, st->gs + 5 * n);
@@ -561,8 +597,10 @@ void ORC(step)(orc_state* st, long nsteps) {
       for (int x = 0; x < nx; ++x) {
         int n = y * nx + x;
         real_t fo[9], gfo[5], gso[5];
-        node_collide(st, n, st->f + 9 * n, st->gf + 5 * n, st->gs + 5 * n, fo, gfo, gso, NULL,
+        node_macro mo;
+        node_collide(st, n, st->f + 9 * n, st->gf + 5 * n, st->gs + 5 * n, fo, gfo, gso, &mo,
                      NULL, NULL);
+        st->um_next[n] = sqrt(RE(mo.ux) * RE(mo.ux) + RE(mo.uy) * RE(mo.uy));
         for (int i = 0; i < 9; ++i) {
           int tx = x + st->lat.ex[i], ty = y + st->lat.ey[i];
           if (px) tx = wrap(tx, nx);
@@ -582,6 +620,11 @@ void ORC(step)(orc_state* st, long nsteps) {
     real_t* t1 = st->f; st->f = st->fn; st->fn = t1;
     real_t* t2 = st->gf; st->gf = st->gfn; st->gfn = t2;
     real_t* t3 = st->gs; st->gs = st->gsn; st->gsn = t3;
+    if (p->hv_local) {
+      /* the new state's temperature solves use |u| of the state just collided */
+      double* t4 = st->um; st->um = st->um_next; st->um_next = t4;
+      for (int n = 0; n < st->nn; ++n) st->hv[n] = hv_of(st, st->um[n]);
+    }
     apply_walls(st);
     ++st->step;
   }

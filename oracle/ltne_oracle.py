@@ -56,6 +56,7 @@ class OracleParams(C.Structure):
         ("zeta_e", C.c_double), ("zeta_nu", C.c_double), ("eta_e", C.c_double),
         ("eta_nu", C.c_double), ("varpi", C.c_double),
         ("ext_ax", C.c_double), ("ext_ay", C.c_double), ("nu_override", C.c_double),
+        ("hv_local", C.c_int32), ("thermal_correction", C.c_int32), ("Dp_over_L", C.c_double),
         ("L_ref", C.c_double),
     ]
 
@@ -66,7 +67,8 @@ class OracleParams(C.Structure):
         gamma_sf=1.0, sigma=1.0, J_e=1.0, T_hot=1.0, T_cold=0.0, T_ref=0.5, Ma=0.1,
         F_phi=-1.0, d_p=0.0, qf=0.0, qs=0.0, s_e=1.1, s_eps=1.1, s_q=1.2,
         zeta_e=1.1, zeta_nu=1.1, eta_e=1.1, eta_nu=1.1, varpi=0.4,
-        ext_ax=0.0, ext_ay=0.0, nu_override=0.0, L_ref=0.0,
+        ext_ax=0.0, ext_ay=0.0, nu_override=0.0, hv_local=0, thermal_correction=0, Dp_over_L=0.0135,
+        L_ref=0.0,
     )
 
     @classmethod

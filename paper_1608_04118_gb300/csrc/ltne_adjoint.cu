@@ -546,7 +546,7 @@ int ltne_adjoint(ltne_handle* h, const double* porosity, const double* rho, cons
     return LTNE_ERR_INVALID_ARG;
   if (!h->ws) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;
-  if (p.bc != LTNE_BC_CAVITY || !p.porosity_field ||
+  if (p.bc != LTNE_BC_CAVITY || !p.porosity_field || p.hv_local ||
       (p.storage != LTNE_F32 && p.storage != LTNE_F64) || p.T_hot == p.T_cold)
     return LTNE_ERR_INVALID_ARG;
   if (bytes < ltne_adjoint_workspace_bytes(h, n_steps, segment) ||

@@ -279,6 +279,13 @@ LTNE_HD void collide_adjoint(const NodeParams<C>& P, const Medium<C>& md, const 
     mb.uy += P.zeta_a * Tf * ip * nb2;
     mb.dTf += P.zeta_a * ip * (ux * nb1 + uy * nb2);
     mb.inv_phi += P.zeta_a * Tf * (ux * nb1 + uy * nb2);
+    if (P.tcorr) {  // ns1 += cw Fx, ns2 += cw Fy, cw = (1 - zeta_a/2) T_f / phi
+      const C c = C(1) - C(0.5) * P.zeta_a;
+      mb.Fx += c * Tf * ip * nb1;
+      mb.Fy += c * Tf * ip * nb2;
+      mb.dTf += c * ip * (Fx * nb1 + Fy * nb2);
+      mb.inv_phi += c * Tf * (Fx * nb1 + Fy * nb2);
+    }
     const C n3_b = (C(1) - P.zeta_e) * nb3;
     mb.dTf += P.zeta_e * P.c3 * nb3;
     mb.Srf += (C(1) - C(0.5) * P.zeta_e) * P.c3 * nb3;

@@ -115,6 +115,7 @@ int derive_params(const ltne_params& p, const double* porosity, NodeParams<doubl
       }
       d = L * sqrt(150.0 * p.Da / acc);
     }
+    info.d_ergun = d;
     P.erg_a = 150.0 * nu_f / (d * d);
     P.erg_b = 1.75 / d;
     P.erg_c = P.Fconst * sqrt(150.0) / d;
@@ -140,6 +141,16 @@ int derive_params(const ltne_params& p, const double* porosity, NodeParams<doubl
     }
     m.l0 = 0.5 * (1.0 + 0.5 * ph * m.c0);                // Eq. 22
     m.l1 = 0.5 * ph * m.c1;
+    m.inv_oms = 1.0 / ((1.0 - ph) * p.sigma);
+  }
+  // Local h_v (Eq. 52): h_v/(rho c)_f = H_p alpha_f / D_p^2 with
+  // H_p = 0.376 (u_m D_p / nu_f)^0.644 Pr^0.37.
+  P.hv_local = p.hv_local ? 1 : 0;
+  P.tcorr = p.thermal_correction ? 1 : 0;
+  {
+    const double Dp = p.Dp_over_L * L;
+    P.hv_c = p.hv_local ? 0.376 * pow(p.Pr, 0.37) * pow(Dp / nu_f, 0.644) * alpha_f / (Dp * Dp)
+                        : 0.0;
   }
   const double rates[] = {P.s_e, P.s_eps, P.s_q, P.s_nu, P.zeta_a, P.zeta_e,
                           P.zeta_nu, P.eta_a, P.eta_e, P.eta_nu};
@@ -164,6 +175,9 @@ int validate_params(const ltne_params& p) {
   if (!in_open(p.varpi, 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
   if (!(p.Pr > 0) || !(p.sigma > 0) || !(p.J_e > 0) || !(p.gamma_sf > 0)) return LTNE_ERR_INVALID_ARG;
   if (!(p.Da > 0) || !(p.Ma > 0) || !(p.H >= 0) || !(p.Ra >= 0)) return LTNE_ERR_INVALID_ARG;
+  if (p.hv_local != 0 && p.hv_local != 1) return LTNE_ERR_INVALID_ARG;
+  if (p.thermal_correction != 0 && p.thermal_correction != 1) return LTNE_ERR_INVALID_ARG;
+  if (p.hv_local && !(p.Dp_over_L > 0 && isfinite(p.Dp_over_L))) return LTNE_ERR_INVALID_ARG;
   const double vals[] = {p.Ra, p.Pr, p.Da, p.H, p.gamma_sf, p.sigma, p.J_e, p.T_hot, p.T_cold,
                          p.T_ref, p.Ma, p.F_phi, p.d_p, p.qf, p.qs, p.ext_ax, p.ext_ay,
                          p.nu_override};
@@ -218,6 +232,7 @@ int derive(ltne_handle* h, const double* porosity) {
     h->L = info.L;
     h->nu_f = info.nu_f;
     h->alpha_f = info.alpha_f;
+    h->d_ergun = info.d_ergun;
   }
   return rc;
 }
@@ -247,6 +262,10 @@ void layout(ltne_handle* h) {
   off = align_up(off + NACC * sizeof(double), A);
   h->off_tick = off;  // two uint32 step counters for the stochastic rounding
   off = align_up(off + 2 * sizeof(uint32_t), A);
+  for (int b = 0; b < 2; ++b) {  // |u| of the previous state per buffer (Eq. 52)
+    h->off_um[b] = off;
+    if (p.hv_local) off = align_up(off + (size_t)h->plane * h->ec, A);
+  }
   h->ws_bytes = off;
   h->enc_scale = p.storage == LTNE_F16DEV ? 1024.0f : 1.0f;  // FP16 deviations x 2^10
 }
@@ -267,6 +286,10 @@ LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
   uint32_t* tick = reinterpret_cast<uint32_t*>(h->ws + h->off_tick);
   a.tick_in = tick + src_buf;
   a.tick_out = tick + (src_buf ^ 1);
+  if (h->p.hv_local) {
+    a.um_in = h->ws + h->off_um[src_buf];
+    a.um_out = h->ws + h->off_um[src_buf ^ 1];
+  }
   return a;
 }
 
@@ -450,6 +473,8 @@ void ltne_default_params(ltne_params* p, int32_t nx, int32_t ny) {
   p->eta_e = 1.1;
   p->eta_nu = 1.1;
   p->varpi = 0.4;
+  p->hv_local = 0;
+  p->Dp_over_L = 0.0135;  // Sec. 4
 }
 
 int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
@@ -563,18 +588,24 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
   return LTNE_OK;
 }
 
-// State blob: 64-byte header, then the current populations (19 planes) and
-// the macroscopic planes (5), in the device layout.
+// State blob: 64-byte header (magic, storage, nx, ny, step, plane, Ergun
+// diameter in use), then in the device layout the current populations (19
+// planes), the macroscopic planes (5), the |u| plane of the local h_v model
+// (if on) and the porosity plane (if per node).
 size_t ltne_state_bytes(const ltne_handle* h) {
   if (!h) return 0;
-  return 64 + 19 * (size_t)h->plane * h->es + 5 * (size_t)h->plane * h->ec;
+  return 64 + 19 * (size_t)h->plane * h->es + 5 * (size_t)h->plane * h->ec +
+         (h->p.hv_local ? (size_t)h->plane * h->ec : 0) +
+         (h->p.porosity_field ? (size_t)h->plane * h->ec : 0);
 }
 
 int ltne_get_state(ltne_handle* h, void* host, size_t bytes) {
   if (!h || !host || bytes < ltne_state_bytes(h)) return LTNE_ERR_INVALID_ARG;
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  uint64_t dbits = 0;  // the Ergun diameter in use travels with the porosity
+  memcpy(&dbits, &h->d_ergun, sizeof(dbits));
   uint64_t hdr[8] = {kStateMagic, (uint64_t)h->p.storage, (uint64_t)h->p.nx,
-                     (uint64_t)h->p.ny, (uint64_t)h->step, (uint64_t)h->plane, 0, 0};
+                     (uint64_t)h->p.ny, (uint64_t)h->step, (uint64_t)h->plane, dbits, 0};
   memcpy(host, hdr, sizeof(hdr));
   char* dst = static_cast<char*>(host) + 64;
   const size_t pb = 19 * (size_t)h->plane * h->es, mb = 5 * (size_t)h->plane * h->ec;
@@ -582,6 +613,13 @@ int ltne_get_state(ltne_handle* h, void* host, size_t bytes) {
                                   h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dst + pb, h->ws + h->off_mac, mb, cudaMemcpyDeviceToHost, h->stream);
+  const size_t ub = h->p.hv_local ? (size_t)h->plane * h->ec : 0;
+  if (e == cudaSuccess && ub)
+    e = cudaMemcpyAsync(dst + pb + mb, h->ws + h->off_um[h->cur], ub, cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess && h->p.porosity_field)
+    e = cudaMemcpyAsync(dst + pb + mb + ub, h->ws + h->off_phi, (size_t)h->plane * h->ec,
+                        cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return fail_cuda(e);
 }
@@ -600,6 +638,24 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
                                   h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws + h->off_mac, src + pb, mb, cudaMemcpyHostToDevice, h->stream);
+  const size_t ub = h->p.hv_local ? (size_t)h->plane * h->ec : 0;
+  if (e == cudaSuccess && ub)
+    e = cudaMemcpyAsync(h->ws + h->off_um[0], src + pb + mb, ub, cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess && h->p.porosity_field) {
+    e = cudaMemcpyAsync(h->ws + h->off_phi, src + pb + mb + ub, (size_t)h->plane * h->ec,
+                        cudaMemcpyHostToDevice, h->stream);
+    // the lattice constants that depend on the porosity field: the Ergun
+    // diameter is taken from the checkpoint, not re-derived
+    double d = 0.0;
+    memcpy(&d, &hdr[6], sizeof(d));
+    if (h->p.permeability == LTNE_K_ERGUN && h->p.d_p <= 0 && d > 0) {
+      h->p.d_p = d;
+      const int rc = derive(h, nullptr);
+      if (rc != LTNE_OK) return rc;
+      drop_graphs(h);
+    }
+  }
   const uint32_t tick = (uint32_t)hdr[4];  // the rounding stream is keyed by the step
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws + h->off_tick, &tick, sizeof(tick), cudaMemcpyHostToDevice, h->stream);

@@ -199,7 +199,9 @@ int ltne_batch_create(const ltne_params* params, int32_t count, void* cuda_strea
   for (int c = 0; c < count; ++c) {
     const ltne_params& p = b->p[c];
     int rc = validate_params(p);
-    if (rc == LTNE_OK && (p.storage != LTNE_F32 || p.bc != LTNE_BC_CAVITY || p.porosity_field))
+    if (rc == LTNE_OK &&
+        (p.storage != LTNE_F32 || p.bc != LTNE_BC_CAVITY || p.porosity_field || p.hv_local ||
+         p.thermal_correction))
       rc = LTNE_ERR_INVALID_ARG;  // the batched form is FP32 cavities with uniform porosity
     if (rc == LTNE_OK) rc = derive_params(p, nullptr, b->Pd[c], b->info[c]);
     if (rc != LTNE_OK) {
@@ -306,6 +308,9 @@ int ltne_batch_set_fields(ltne_batch* b) {
     a.enc_scale = 1.0f;
     a.tick_in = nullptr;
     a.tick_out = nullptr;
+    a.pre_out = nullptr;
+    a.um_in = nullptr;
+    a.um_out = nullptr;
     e = launch_init_f32(a, b->Pd[c], b->stream);
   }
   if (e != cudaSuccess) return fail_cuda(e);

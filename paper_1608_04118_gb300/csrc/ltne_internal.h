@@ -28,6 +28,8 @@ struct LatticeArgs {
   const uint32_t* tick_in;  // step counter slot read by this step (16-bit forms)
   uint32_t* tick_out;       // slot receiving the next step's counter
   void* pre_out;            // k_init: also record S_0 here (compute type), or nullptr
+  const void* um_in;        // |u| plane of the previous state (local h_v), or nullptr
+  void* um_out;             // |u| plane written for the next state
 };
 
 // Launch configuration of the step kernel (chosen by the autotuner).
@@ -74,6 +76,7 @@ cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
 // the batched form.
 struct DerivedInfo {
   double L = 0, nu_f = 0, alpha_f = 0;
+  double d_ergun = 0;  // Ergun particle diameter in use (0: Darcy permeability)
 };
 int validate_params(const ltne_params& p);
 int derive_params(const ltne_params& p, const double* porosity, NodeParams<double>& P,
@@ -92,12 +95,13 @@ struct ltne_handle {
   ltne::NodeParams<double> P{};
   ltne::StepShape shape;
   // derived lattice values
-  double L = 0, nu_f = 0, alpha_f = 0;
+  double L = 0, nu_f = 0, alpha_f = 0, d_ergun = 0;
   // layout
   int64_t pitch = 0, plane = 0;
   size_t es = 0, ec = 0;  // storage / compute element sizes
   size_t off_pop[2] = {0, 0}, off_phi = 0, off_mac = 0, off_prev = 0, off_part = 0, off_out = 0;
   size_t off_tick = 0;
+  size_t off_um[2] = {0, 0};  // |u| planes (local h_v of Eq. 52)
   size_t ws_bytes = 0;
   char* ws = nullptr;
   int red_blocks = 1;

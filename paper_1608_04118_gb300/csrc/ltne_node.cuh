@@ -36,6 +36,7 @@ namespace ltne {
 template <typename C>
 struct Medium {
   C phi, inv_phi, a, b, inv_1d, c0, c1, l0, l1;
+  C inv_oms;  // 1 / ((1 - phi) sigma)
 };
 
 // Lattice constants in compute type C, built from the paper's values.
@@ -64,6 +65,11 @@ struct NodeParams {
   int kmode;                        // 0 Darcy, 1 Ergun
   int fmode;                        // 0 constant, 1 Ergun
   Medium<C> um;                     // the coefficients at the uniform porosity
+  // Local h_v of Eq. 52: h_v/(rho c)_f = hv_c |u_prev|^0.644 with
+  // hv_c = 0.376 Pr^0.37 (D_p/nu_f)^0.644 alpha_f / D_p^2.
+  int hv_local;
+  C hv_c;
+  int tcorr;  // correction term of Sec. 3.2 on (N C~ = (0, T_f F/phi, 0, 0))
 };
 
 template <typename C>
@@ -135,8 +141,9 @@ LTNE_HD Medium<C> medium_at(const NodeParams<C>& P, C phi) {
   Medium<C> md;
   md.phi = phi;
   md.inv_phi = rcp_<C>(phi);
+  md.inv_oms = rcp_<C>((C(1) - phi) * P.sigma);
   md.a = P.hcoef * md.inv_phi;
-  md.b = P.hcoef * rcp_<C>((C(1) - phi) * P.sigma);
+  md.b = P.hcoef * md.inv_oms;
   md.inv_1d = rcp_<C>(C(1) + C(0.5) * md.a + C(0.5) * md.b);
   if (P.kmode == 0) {
     md.c0 = P.nu_over_K;
@@ -158,6 +165,26 @@ LTNE_HD Medium<C> medium_at(const NodeParams<C>& P, C phi) {
   md.l0 = C(0.5) * (C(1) + C(0.5) * phi * md.c0);  // Eq. 22
   md.l1 = C(0.5) * phi * md.c1;
   return md;
+}
+
+// h_v / (rho c)_f from the correlation of Eq. 52 at a node whose previous
+// velocity magnitude is um.
+template <typename C>
+LTNE_HD C hv_local_at(const NodeParams<C>& P, C um) {
+  if (!(um > C(0))) return C(0);
+#ifdef __CUDA_ARCH__
+  return P.hv_c * exp2(C(0.644) * log2(um));
+#else
+  return P.hv_c * pow(um, C(0.644));
+#endif
+}
+
+// The exchange-dependent coefficients of md with a node-local h_v.
+template <typename C>
+LTNE_HD void set_exchange(Medium<C>& md, C hv) {
+  md.a = hv * md.inv_phi;
+  md.b = hv * md.inv_oms;
+  md.inv_1d = rcp_<C>(C(1) + C(0.5) * md.a + C(0.5) * md.b);
 }
 
 // Macroscopic values of a node from its pre-collision deviations:
@@ -283,8 +310,15 @@ LTNE_HD void collide(const NodeParams<C>& P, const Macro<C>& m, C (&f)[9],
     const C n3 = C(-4) * gf[0] + ((gf[1] + gf[2]) + (gf[3] + gf[4]));
     const C n4 = (gf[1] - gf[2]) + (gf[3] - gf[4]);
     const C ns0 = m.sgf + Srf;  // = T_f + Sr_f / 2 (Eq. 41)
-    const C ns1 = n1 - P.zeta_a * (n1 - ux * Tf * ip);
-    const C ns2 = n2 - P.zeta_a * (n2 - uy * Tf * ip);
+    C ns1 = n1 - P.zeta_a * (n1 - ux * Tf * ip);
+    C ns2 = n2 - P.zeta_a * (n2 - uy * Tf * ip);
+    if (P.tcorr) {
+      // (I - Q/2) N C~ with C~_i = w~_i T_f (e_i.F)/(phi c_sT^2): only the
+      // first-order moments are non-zero, T_f F/phi (sum_i w~_i e_i e_i = c_sT^2).
+      const C cw = (C(1) - C(0.5) * P.zeta_a) * Tf * ip;
+      ns1 += cw * Fx;
+      ns2 += cw * Fy;
+    }
     const C ns3 = n3 - P.zeta_e * (n3 - P.c3 * m.dTf) + (C(1) - C(0.5) * P.zeta_e) * P.c3 * Srf;
     const C ns4 = n4 - P.zeta_nu * n4;
     const C t0 = div_small<C>(ns0, C(5), C(0.2)), t1 = ns1 * C(0.5), t2 = ns2 * C(0.5);

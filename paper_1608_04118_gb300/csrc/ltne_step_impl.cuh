@@ -38,6 +38,8 @@ __host__ NodeParams<C> cast_params(const NodeParams<double>& d) {
   p.um.phi = C(d.um.phi); p.um.inv_phi = C(d.um.inv_phi); p.um.a = C(d.um.a);
   p.um.b = C(d.um.b); p.um.inv_1d = C(d.um.inv_1d); p.um.c0 = C(d.um.c0);
   p.um.c1 = C(d.um.c1); p.um.l0 = C(d.um.l0); p.um.l1 = C(d.um.l1);
+  p.um.inv_oms = C(d.um.inv_oms);
+  p.hv_local = d.hv_local; p.hv_c = C(d.hv_c); p.tcorr = d.tcorr;
   return p;
 }
 
@@ -123,7 +125,9 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
                                           const int nx, const int ny, const int64_t pitch,
                                           const int64_t plane, const C scale, const C inv_scale,
                                           const int write_macros, const uint32_t tick,
-                                          C* __restrict__ pre_out = nullptr) {
+                                          C* __restrict__ pre_out = nullptr,
+                                          const C* __restrict__ um_in = nullptr,
+                                          C* __restrict__ um_out = nullptr) {
   // Wall classification and the node whose neighbourhood is pulled.
   int cx = x, cy = y;
   int kind = -1;  // -1 interior, 0 hot wall, 1 cold wall, 2 adiabatic / no-slip row
@@ -158,8 +162,9 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
 
   const uint32_t off = (uint32_t)y * (uint32_t)pitch + (uint32_t)x;
   if (BC != BC_PERIODIC && kind >= 0) {
-    const Medium<C> mdn =
-        phi_field ? medium_at<C>(P, phi_field[(uint32_t)cy * (uint32_t)pitch + (uint32_t)cx]) : P.um;
+    const uint32_t noff = (uint32_t)cy * (uint32_t)pitch + (uint32_t)cx;
+    Medium<C> mdn = phi_field ? medium_at<C>(P, phi_field[noff]) : P.um;
+    if (P.hv_local) set_exchange<C>(mdn, hv_local_at<C>(P, um_in[noff]));
     Macro<C> mn;
     macros<C>(P, mdn, f, gf, gs, mn);
     C dTwf = mn.dTf, dTws = mn.dTs;  // adiabatic: the neighbour's temperature
@@ -175,9 +180,11 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
 #pragma unroll
     for (int i = 0; i < 5; ++i) pre_out[(int64_t)(14 + i) * plane + off] = gs[i];
   }
-  const Medium<C> md = phi_field ? medium_at<C>(P, phi_field[off]) : P.um;
+  Medium<C> md = phi_field ? medium_at<C>(P, phi_field[off]) : P.um;
+  if (P.hv_local) set_exchange<C>(md, hv_local_at<C>(P, um_in[off]));
   Macro<C> m;
   macros<C>(P, md, f, gf, gs, m);
+  if (P.hv_local) um_out[off] = m.umag;  // u_m of Eq. 52 for the next state
   if (write_macros) store_macros<C>(mac, plane, off, m);
   collide<C>(P, m, f, gf, gs);
   Pops<S, C>::store(dst, plane, off, scale, f, gf, gs, (uint32_t)off, tick);
@@ -206,13 +213,15 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
                                               const int64_t plane, const C scale,
                                               const C inv_scale, const int write_macros,
                                               const uint32_t* __restrict__ tick_in,
-                                              uint32_t* __restrict__ tick_out) {
+                                              uint32_t* __restrict__ tick_out,
+                                              const C* __restrict__ um_in,
+                                              C* __restrict__ um_out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t tick = read_tick<S, C>(tick_in, tick_out);
   if (x >= nx || y >= ny) return;
   step_node<S, C, BC>(src, dst, phi_field, mac, P, x, y, nx, ny, pitch, plane, scale, inv_scale,
-                      write_macros, tick);
+                      write_macros, tick, nullptr, um_in, um_out);
 }
 
 // S_0 from the fields held in the macro planes (rho, ux, uy, Tf, Ts), then
@@ -223,12 +232,16 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ dst,
                                               C* __restrict__ mac, const NodeParams<C> P,
                                               const int nx, const int ny, const int64_t pitch,
                                               const int64_t plane, const C scale,
-                                              C* __restrict__ pre_out) {
+                                              C* __restrict__ pre_out, C* __restrict__ um_out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int64_t off = (int64_t)y * pitch + x;
-  const Medium<C> md = phi_field ? medium_at<C>(P, phi_field[off]) : P.um;
+  Medium<C> md = phi_field ? medium_at<C>(P, phi_field[off]) : P.um;
+  if (P.hv_local) {  // u_m of S_0: the initial field's |u|
+    const C ux = mac[plane + off], uy = mac[2 * plane + off];
+    set_exchange<C>(md, hv_local_at<C>(P, sqrt_<C>(ux * ux + uy * uy)));
+  }
   C f[9], gf[5], gs[5];
   equilibrium<C>(P, md.phi, mac[off], mac[plane + off], mac[2 * plane + off],
                  mac[3 * plane + off], mac[4 * plane + off], f, gf, gs);
@@ -242,6 +255,7 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ dst,
   }
   Macro<C> m;
   macros<C>(P, md, f, gf, gs, m);
+  if (P.hv_local) um_out[off] = m.umag;
   store_macros<C>(mac, plane, off, m);
   collide<C>(P, m, f, gf, gs);
   Pops<S, C>::store(dst, plane, off, scale, f, gf, gs, (uint32_t)off, 0xffffffffu);
@@ -258,21 +272,25 @@ cudaError_t launch_step_t(const LatticeArgs& a, const NodeParams<double>& Pd, St
   S* dst = static_cast<S*>(a.dst);
   const C* phi = static_cast<const C*>(a.phi);
   C* mac = static_cast<C*>(a.mac);
+  const C* um_in = static_cast<const C*>(a.um_in);
+  C* um_out = static_cast<C*>(a.um_out);
   switch (a.bc) {
     case BC_CAVITY:
       k_step<S, C, BC_CAVITY><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny, a.pitch,
                                                       a.plane, scale, inv_scale, a.write_macros,
-                                                      a.tick_in, a.tick_out);
+                                                      a.tick_in, a.tick_out, um_in, um_out);
       break;
     case BC_PERIODIC:
       k_step<S, C, BC_PERIODIC><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
                                                         a.pitch, a.plane, scale, inv_scale,
-                                                        a.write_macros, a.tick_in, a.tick_out);
+                                                        a.write_macros, a.tick_in, a.tick_out,
+                                                        um_in, um_out);
       break;
     case BC_CHANNEL:
       k_step<S, C, BC_CHANNEL><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
                                                        a.pitch, a.plane, scale, inv_scale,
-                                                       a.write_macros, a.tick_in, a.tick_out);
+                                                       a.write_macros, a.tick_in, a.tick_out,
+                                                       um_in, um_out);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -287,7 +305,8 @@ cudaError_t launch_init_t(const LatticeArgs& a, const NodeParams<double>& Pd, cu
   dim3 grid((a.nx + 127) / 128, (a.ny + 1) / 2);
   k_init<S, C><<<grid, block, 0, st>>>(static_cast<S*>(a.dst), static_cast<const C*>(a.phi),
                                        static_cast<C*>(a.mac), P, a.nx, a.ny, a.pitch, a.plane,
-                                       C(a.enc_scale), static_cast<C*>(a.pre_out));
+                                       C(a.enc_scale), static_cast<C*>(a.pre_out),
+                                       static_cast<C*>(a.um_out));
   return cudaGetLastError();
 }
 

@@ -53,6 +53,7 @@ class ltne_params(C.Structure):
         ("zeta_e", C.c_double), ("zeta_nu", C.c_double), ("eta_e", C.c_double),
         ("eta_nu", C.c_double), ("varpi", C.c_double),
         ("ext_ax", C.c_double), ("ext_ay", C.c_double), ("nu_override", C.c_double),
+        ("hv_local", C.c_int32), ("thermal_correction", C.c_int32), ("Dp_over_L", C.c_double),
     ]
 
 

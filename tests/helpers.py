@@ -4,7 +4,8 @@ import numpy as np
 
 PHYS_KEYS = ("Ra", "Pr", "Da", "porosity", "H", "gamma_sf", "sigma", "J_e", "T_hot", "T_cold",
              "T_ref", "Ma", "F_phi", "d_p", "qf", "qs", "s_e", "s_eps", "s_q", "zeta_e",
-             "zeta_nu", "eta_e", "eta_nu", "varpi", "ext_ax", "ext_ay", "nu_override")
+             "zeta_nu", "eta_e", "eta_nu", "varpi", "ext_ax", "ext_ay", "nu_override",
+             "hv_local", "Dp_over_L", "thermal_correction")
 
 
 def phys(d):

@@ -124,3 +124,40 @@ def test_workspace_size_and_state_calls_without_gpu(lt):
     finally:
         lt.ltne_destroy(h)
     assert lt.ltne_error_string(lt.LTNE_ERR_UNSTABLE_TAU).startswith("LTNE_ERR_UNSTABLE_TAU")
+
+
+def test_option_validation_without_gpu(lt):
+    import ctypes as C
+
+    lib = lt.load()
+    # local h_v needs a positive D_p / L; switches are 0 or 1
+    assert _create(lt, hv_local=1) == lt.LTNE_OK
+    assert _create(lt, hv_local=1, Dp_over_L=0.0) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, hv_local=2) == lt.LTNE_ERR_INVALID_ARG
+    assert _create(lt, thermal_correction=1) == lt.LTNE_OK
+    assert _create(lt, thermal_correction=-1) == lt.LTNE_ERR_INVALID_ARG
+    # the batched form is FP32 cavities with uniform porosity and neither option
+    for kw in (dict(hv_local=1), dict(thermal_correction=1), dict(storage=lt.LTNE_F64),
+               dict(porosity_field=1), dict(bc=lt.LTNE_BC_PERIODIC)):
+        arr = (lt.ltne_params * 2)(lt.ltne_default_params(32, 32),
+                                   lt.ltne_default_params(48, 32, **kw))
+        b = C.c_void_p()
+        assert lib.ltne_batch_create(arr, 2, None, C.byref(b)) == lt.LTNE_ERR_INVALID_ARG, kw
+    arr = (lt.ltne_params * 2)(lt.ltne_default_params(32, 32), lt.ltne_default_params(64, 32))
+    b = C.c_void_p()
+    assert lib.ltne_batch_create(arr, 2, None, C.byref(b)) == lt.LTNE_OK
+    assert lt.ltne_batch_nodes(b) == 32 * 32 + 64 * 32
+    assert lt.ltne_batch_workspace_bytes(b) > 2 * 19 * 4 * (32 * 32 + 64 * 32)
+    # a schedule needs a bound workspace
+    assert lib.ltne_batch_set_schedule(b, 64, 2, 0) == lt.LTNE_ERR_STATE
+    lt.ltne_batch_destroy(b)
+    # the adjoint needs a bound workspace and rejects the local h_v model
+    p = lt.ltne_default_params(32, 32, porosity_field=1, hv_local=1)
+    h = lt.ltne_create(p)
+    J, dH = C.c_double(), C.c_double()
+    phi = (C.c_double * (32 * 32))(*([0.5] * (32 * 32)))
+    assert lib.ltne_adjoint(h, phi, None, None, None, 10, 4, C.c_void_p(256), 1 << 20, None,
+                            C.byref(J), C.byref(dH)) == lt.LTNE_ERR_STATE
+    assert lt.ltne_adjoint_workspace_bytes(h, 100, 10) > 0
+    assert lt.ltne_adjoint_workspace_bytes(h, 0, 10) == 0
+    lt.ltne_destroy(h)

@@ -207,3 +207,43 @@ def _c5_oracle(cfg):
         o = oracle_for(cfg).init().step(cfg["steps"])
         _C5_CACHE["ref"] = {"fields": o.macros(), "obs": o.observables()}
     return _C5_CACHE["ref"]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_local_heat_transfer_coefficient_eq52(storage):
+    """Per-node h_v from the correlation of Eq. 52 (H_p = 0.376 Re^0.644
+    Pr^0.37, Re = u_m D_p / nu_f, D_p = 0.0135 L) with u_m the node's |u| in
+    the previous state, from random initial fields (so the initial |u|
+    matters), per-node porosity and the paper's validation parameters
+    (phi around 0.8, F_phi 0.068, gamma_sf 1000, T_h 11, T_c = T_0 = 1)."""
+    nx, ny = 41, 37
+    cfg = dict(nx=nx, ny=ny, Ra=1e6, Pr=1.0, Da=1e-4, porosity=0.8, gamma_sf=1000.0, sigma=1.0,
+               T_hot=11.0, T_cold=1.0, T_ref=1.0, F_phi=0.068, hv_local=1, Dp_over_L=0.0135,
+               ergun=True)
+    phi = W.porosity_field(nx, ny, 0.7, 0.9, seed=14).reshape(-1)
+    fields = W.random_fields(nx, ny, 114, du=0.02, dT=0.3)
+    fields["T_f"] = fields["T_f"] + 0.5
+    fields["T_s"] = fields["T_s"] + 0.5
+    c, o = run_pair(cfg, 400, storage, phi=phi, fields=fields)
+    err = field_errors(c.fields(), o.macros())
+    for k in ("u", "Tf", "Ts"):
+        assert err[k] <= TOL[storage] * (1 if storage == "f64" else 3), (k, err)
+    blob = c.get_state()
+    c.step(50)
+    d = cavity_for(cfg, storage=storage, phi=phi).set_state(blob).step(50)
+    fa, fb = c.fields(), d.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_thermal_correction_term(storage):
+    """The correction term of Sec. 3.2 (off by default, as in the paper)
+    switched on, in a convecting cavity with per-node porosity."""
+    cfg = dict(W.random_params(15, 29, 27), thermal_correction=1, ergun=True)
+    phi = W.porosity_field(29, 27, 0.4, 0.85, seed=16).reshape(-1)
+    fields = W.random_fields(29, 27, 116)
+    c, o = run_pair(cfg, 300, storage, phi=phi, fields=fields)
+    err = field_errors(c.fields(), o.macros())
+    for k in ("u", "Tf", "Ts"):
+        assert err[k] <= TOL[storage] * (1 if storage == "f64" else 2), (k, err)

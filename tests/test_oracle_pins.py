@@ -455,3 +455,40 @@ def test_internal_generation_uniform_box():
     o.step(5000)
     mac = o.macros()
     assert np.allclose(mac["Tf"] - mac["Ts"], (qf - qs) / k, rtol=1e-9)
+
+
+# ---------------------------------------------------------------- f2 -----
+@pytest.mark.parametrize("Pr", [5.0, 1.0])
+def test_correction_term_removes_the_unwanted_flux(Pr):
+    """Sec. 3.2 (Eq. 47): the thermal equation carries an unwanted flux
+    (1/zeta_alpha - 1/2) d_t1(u T_f / phi); under a uniform force with no
+    pressure gradient d_t1 u = F, so a temperature profile advected by the
+    accelerating flow drifts by -(1/zeta_alpha - 1/2) sum_n F/phi against the
+    exact displacement integral of u/phi dt.  The correction term
+    dt N^-1 (I - Q/2) C with C~_i = w~_i T_f (e_i.F)/(phi c_sT^2) removes it."""
+    nx, ny, N, A, phi = 64, 3, 300, 2e-5, 0.7
+    x = np.arange(nx)
+    k = 2 * np.pi / nx
+    drift = {}
+    for tc in (0, 1):
+        o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=0.0, nu_override=0.1, Pr=Pr,
+                                     Da=1e6, porosity=phi, F_phi=0.0, ext_ax=A, H=0.0,
+                                     T_hot=0.5, T_cold=0.5, thermal_correction=tc))
+        o.init(Tf=np.tile(0.5 + 0.1 * np.sin(k * x), ny), Ts=np.full(nx * ny, 0.5))
+        c = 1 / o.derived()["zeta_alpha"] - 0.5
+
+        def phase():
+            t = o.macros()["Tf"][1] - 0.5
+            return np.angle(np.sum(t * np.exp(-1j * k * x)))
+
+        p0 = phase()
+        u = [o.macros()["ux"][1].mean()]
+        for _ in range(N):
+            o.step(1)
+            u.append(o.macros()["ux"][1].mean())
+        u = np.array(u)
+        X_exact = np.sum(0.5 * (u[1:] + u[:-1])) / phi  # u is linear in time here
+        drift[tc] = -(phase() - p0) / k - X_exact
+    F_over_phi_sum = A * N
+    assert drift[0] == pytest.approx(-c * F_over_phi_sum, rel=0.15)
+    assert abs(drift[1]) <= 0.15 * c * F_over_phi_sum
