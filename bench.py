@@ -46,6 +46,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096, help="cavity side (nodes)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
+    ap.add_argument("--npt", type=int, default=0, choices=[0, 1, 2],
+                    help="nodes per thread of the step kernel (0: the library default)")
+    ap.add_argument("--block", default="",
+                    help="block shape bx,by of the step kernel (default: the library's)")
+    ap.add_argument("--cavities", type=int, default=256,
+                    help="c3: number of cavities (the workload has 256; fewer for profiling)")
+    ap.add_argument("--batch-schedule", default="",
+                    help="c3: tile_x,tile_y,blocks instead of the autotuned schedule")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -108,9 +116,10 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(storage, n):
-    """ncu DRAM bytes per launch of the step kernel from the committed
-    profile summary, if it was taken on the current kernel source."""
+def kernel_traffic(storage, n, npt):
+    """ncu DRAM bytes per launch of the step kernel (storage type, nodes per
+    thread) from the committed profile summary, if it was taken on the
+    current kernel source."""
     p = os.path.join(ROOT, "profiles", "step_traffic.json")
     if not os.path.exists(p):
         return None
@@ -121,7 +130,7 @@ def kernel_traffic(storage, n):
 
         if d.get("source_hash") != B.kernel_source_hash():
             return None
-        e = d["entries"].get(storage)
+        e = d["entries"].get("%s/npt%d" % (storage, npt))
         if not e:
             return None
         # traffic grows with the node count; scale the captured case
@@ -253,11 +262,15 @@ def run_batch(args):
     from paper_1608_04118_gb300.autotune import tune_batch
     from paper_1608_04118_gb300.ltne import Batch, Cavity
 
-    cavs = W.batch_cavities(256, seed=3)
+    cavs = W.batch_cavities(256, seed=3)[:args.cavities]
     stream = torch.cuda.Stream()
     b = Batch(cavs, stream=stream)
     t0 = time.perf_counter()
-    sched, t_best, table = tune_batch(b, steps=4, warmup=2)
+    if args.batch_schedule:
+        sched, table = tuple(int(v) for v in args.batch_schedule.split(",")), []
+        b.set_schedule(*sched)
+    else:
+        sched, t_best, table = tune_batch(b, steps=4, warmup=2)
     tune_s = time.perf_counter() - t0
     b.set_fields()
     with torch.cuda.stream(stream):
@@ -297,8 +310,8 @@ def run_batch(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_launch * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "256 porous LTNE cavities, sides 64..512, aspect 1-2, "
-                                   "seed 3", "nodes": nodes,
+            "config": {"workload": "%d porous LTNE cavities, sides 64..512, aspect 1-2, "
+                                   "seed 3" % len(cavs), "nodes": nodes,
                        "schedule": {"tile_x": sched[0], "tile_y": sched[1],
                                     "blocks": sched[2], "tuning_s": tune_s,
                                     "trials": len(table)}},
@@ -331,22 +344,28 @@ def run_reduced(args):
                               "T_cold", "T_ref")}
     n = args.n if args.n != 4096 else c["nx"]
     stream = torch.cuda.Stream()
-    rates = {}
+    rates, rates_one_node, schedules = {}, {}, {}
     for st in ("f32", "f16", "bf16"):
-        cav = Cavity(n, n, stream=stream, storage=st, **phys).set_fields()
-        with torch.cuda.stream(stream):
-            cav.step(max(args.warmup, 3))
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        cav.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        t = ev0.elapsed_time(ev1) / 1e3
-        rates[st] = n * n * args.steps / t / 1e6
-        cav.close()
-        del cav
-        torch.cuda.empty_cache()
+        for one_node in (False, True):
+            cav = Cavity(n, n, stream=stream, storage=st, **phys)
+            if one_node:
+                cav.set_schedule(128, 2, 1)
+            schedules[(st, one_node)] = cav.schedule
+            cav.set_fields()
+            with torch.cuda.stream(stream):
+                cav.step(max(args.warmup, 3))
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            cav.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t = ev0.elapsed_time(ev1) / 1e3
+            (rates_one_node if one_node else rates)[st] = n * n * args.steps / t / 1e6
+            cav.close()
+            del cav
+            torch.cuda.empty_cache()
     m = c["parity_n"]
     o = Oracle(OracleParams.make(m, m, **phys)).init().step(c["steps"])
     ref, robs = o.macros(), o.observables()
@@ -373,7 +392,8 @@ def run_reduced(args):
             "config": {"workload": "porous LTNE cavity %dx%d, phi 0.6, Da 1e-2, Ra 1e6, H 1000"
                                    % (n, n), "parity_run": "%dx%d, %d steps vs FP64 oracle"
                                                            % (m, m, c["steps"])},
-            "mlups": rates,
+            "mlups": rates, "schedules": {st: list(schedules[(st, False)]) for st in rates},
+            "mlups_one_node_per_thread": rates_one_node,
             "roofline": {st: {"achieved": bpl[st] * rates[st] * 1e6 / 1e9, "peak": peak,
                               "frac": bpl[st] * rates[st] * 1e6 / 1e9 / peak, "unit": "GB/s",
                               "peak_kind": kind} for st in rates},
@@ -476,6 +496,11 @@ def main():
     stream = torch.cuda.Stream(dev)
     cav = Cavity(n, n, stream=stream, storage=args.storage, permeability=LTNE_K_ERGUN,
                  porosity_field=1, **kw)
+    if args.block or args.npt:
+        bx, by = ((int(v) for v in args.block.split(",")) if args.block
+                  else ((128, 2) if args.npt == 1 else (128, 1)))
+        cav.set_schedule(bx, by, args.npt or cav.schedule[2])
+    schedule = cav.schedule
     cav.set_fields(porosity=phi)
 
     def barrier():
@@ -518,18 +543,25 @@ def main():
         barrier()
         t0 = time.perf_counter()
         cav.set_fields(porosity=phi)  # H2D of the porosity and the initial fields
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         cav.step(k)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         host_out = cav.fields()       # D2H of the fields
         host_ob = cav.observables()   # D2H of the observables
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
+        t3 = time.perf_counter()
+        te = t3 - t0
         tt = max_over_ranks(te, dev)
         h2d = phi.nbytes + 5 * nodes * 4  # porosity + five staged fields (compute type)
         d2h = 5 * nodes * 4 + 18 * 8      # five fields + the observables accumulators
         e2e = {"value": whole_job_mlups(nodes, k, ws, tt), "unit": UNIT,
                "h2d_bytes_per_step": h2d / k, "d2h_bytes_per_step": d2h / k,
                "note": "whole run through the C ABI: set_fields from host arrays, %d steps, "
-                       "get_fields + observables to host" % k}
+                       "get_fields + observables to host" % k,
+               "phases_s": {"set_fields": t1 - t0, "steps": t2 - t1,
+                            "get_fields_and_observables": t3 - t2}}
         assert host_ob["nonfinite"] == 0 and np.isfinite(host_out["Tf"]).all()
 
     if rank != 0:
@@ -543,14 +575,18 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.storage == "f64" else "f32", "storage": args.storage,
-        "data": "synthetic", "config": workload_config(n, args.storage),
+        "data": "synthetic",
+        "config": dict(workload_config(n, args.storage),
+                       schedule={"block": [schedule[0], schedule[1]],
+                                 "nodes_per_thread": schedule[2]}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "frac_of_8TBs": achieved / 8000.0,
                      "bytes_per_lup": BYTES_PER_LUP[args.storage],
-                     "traffic": kernel_traffic(args.storage, n),
-                     "kernel": "k_step<%s> (one launch = one step of %d nodes)" % (args.storage,
-                                                                                    nodes)},
+                     "traffic": kernel_traffic(args.storage, n, schedule[2]),
+                     "kernel": "%s<%s> (one launch = one step of %d nodes)"
+                               % ("k_step_pair" if schedule[2] == 2 else "k_step", args.storage,
+                                  nodes)},
         "gpu_launches": int(launches),
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "observables": {"Nu_f_hot": ob["Nu_f_hot"], "Nu_s_hot": ob["Nu_s_hot"],

@@ -69,8 +69,8 @@ enum { LTNE_BC_CAVITY = 0, LTNE_BC_PERIODIC = 1, LTNE_BC_CHANNEL = 2 };
    with d fixed so that the mean of K / L^2 over the nodes equals Da. */
 enum { LTNE_K_DARCY = 0, LTNE_K_ERGUN = 1 };
 
-/* Problem statement.  The dimensionless groups follow Sec. 2 (L73-79 of
-   the paper: Ra, Pr, Da, J_e, gamma_sf, sigma, H_v); relaxation rates and
+/* Problem statement.  The dimensionless groups follow Sec. 2 of the
+   paper (Ra, Pr, Da, J_e, gamma_sf, sigma, H_v); relaxation rates and
    varpi default to the values of Sec. 4.  Lattice mapping (the paper
    leaves the velocity scale open): L = ny - 1, u_c = Ma c_s = sqrt(g beta
    dT L), nu_f = u_c L sqrt(Pr/Ra), alpha_f = nu_f/Pr, nu_e = J_e nu_f,
@@ -136,8 +136,8 @@ typedef struct ltne_obs {
   double max_u;            /* max |u|                                        */
   double max_dT;           /* max |T_f - T_s|                                */
   double mean_Tf, mean_Ts;
-  double Fo;               /* alpha_f t / L^2 (the paper's Fo, L77, read as
-                              a dimensionless time)                          */
+  double Fo;               /* alpha_f t / L^2 (the Fo of Sec. 2, read as a
+                              dimensionless time)                            */
   int64_t step;            /* steps taken since set_fields                   */
   int64_t nonfinite;       /* number of nodes with a non-finite field        */
 } ltne_obs;
@@ -198,6 +198,22 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes);
 
 /* Number of step-kernel launches issued by this handle so far. */
 int64_t ltne_launch_count(const ltne_handle* h);
+
+/* Launch schedule of the step kernel (no counterpart in the paper, which
+   prescribes no implementation): blocks of block_x x block_y threads
+   (block_x a multiple of 32 in 32..256, block_x * block_y <= 256), each
+   thread advancing nodes_per_thread = 1 node or 2 neighbouring nodes of a
+   row in paired FP32 arithmetic (FP32, FP16 and BF16 storage only, and
+   block_x * block_y <= 128).  The schedule changes no result beyond FP32
+   rounding: the arithmetic per node is the same, and for a given
+   nodes_per_thread the block shape changes no bit.  Defaults: 32 x 4 with
+   two nodes per thread (FP16, BF16), 128 x 1 with two (FP32), 128 x 2 with
+   one (FP64).  May be called at any time between steps.
+   LTNE_ERR_INVALID_ARG for other schedules. */
+int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
+                      int32_t nodes_per_thread);
+int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
+                      int32_t* nodes_per_thread);
 
 /* ------------------------------------------------------------------------
  * Adjoint: gradients of J = (Nu_f,hot + Nu_s,hot) / 2 after n_steps steps

@@ -46,3 +46,38 @@ def tune_batch(batch, steps=8, warmup=2):
     best = min(table, key=lambda r: r[1])
     batch.set_schedule(*best[0])
     return best[0], best[1], table
+
+
+# Single-lattice step kernel: block shapes (threads per block <= 256) and
+# nodes per thread (2 = paired FP32 arithmetic, not for FP64 storage).
+CAVITY_SHAPES = ((32, 2), (32, 4), (64, 1), (64, 2), (64, 4), (128, 1), (128, 2), (256, 1))
+
+
+def cavity_candidates(storage):
+    for npt in ((1,) if storage == "f64" else (1, 2)):
+        for bx, by in CAVITY_SHAPES:
+            if npt == 1 or bx * by <= 128:  # the two-node kernel takes <= 128 threads
+                yield bx, by, npt
+
+
+def tune_cavity(cav, steps=20, warmup=4):
+    """Pick the fastest step-kernel schedule for ``cav`` (a ``Cavity`` whose
+    fields are set; the trial steps advance its state).  Returns (schedule,
+    seconds per step, table of all trials)."""
+    import torch
+
+    table = []
+    for sch in cavity_candidates(cav.storage):
+        cav.set_schedule(*sch)
+        with torch.cuda.stream(cav.stream):
+            cav.step(warmup)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(cav.stream)
+            cav.step(steps)
+            e1.record(cav.stream)
+        e1.synchronize()
+        table.append((sch, e0.elapsed_time(e1) / 1e3 / steps))
+    best = min(table, key=lambda r: r[1])
+    cav.set_schedule(*best[0])
+    return best[0], best[1], table

@@ -37,7 +37,7 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _fingerprint() -> str:
+def _fingerprint(extra_flags=()) -> str:
     h = hashlib.sha256()
     files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
         glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
@@ -45,7 +45,7 @@ def _fingerprint() -> str:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + list(extra_flags)).encode())
     return h.hexdigest()
 
 
@@ -53,7 +53,7 @@ def kernel_source_hash() -> str:
     """Hash of the sources that define the step kernel (used to tell whether
     stored profiler counters still describe the current kernel)."""
     h = hashlib.sha256()
-    names = ["ltne_node.cuh", "ltne_step_impl.cuh", "ltne_internal.h"] + sorted(
+    names = ["ltne_node.cuh", "ltne_step_impl.cuh", "ltne_pair.cuh", "ltne_internal.h"] + sorted(
         os.path.basename(f) for f in glob.glob(os.path.join(CSRC, "step_*.cu")))
     for n in names:
         with open(os.path.join(CSRC, n), "rb") as fh:
@@ -63,8 +63,12 @@ def kernel_source_hash() -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile (if sources changed) and return the path of libltne.so."""
-    fp = _fingerprint()
+    """Compile (if sources or flags changed) and return the path of
+    libltne.so.  Extra nvcc flags come from ``extra_flags`` or, if that is
+    None, from the environment variable LTNE_NVCC_FLAGS (space-separated)."""
+    if extra_flags is None:
+        extra_flags = os.environ.get("LTNE_NVCC_FLAGS", "").split()
+    fp = _fingerprint(tuple(extra_flags or ()))
     stamp = LIB + ".stamp"
     if (not force and os.path.exists(LIB) and os.path.exists(stamp)
             and open(stamp).read().strip() == fp):

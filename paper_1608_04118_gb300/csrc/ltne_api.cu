@@ -6,6 +6,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "ltne.h"
@@ -39,6 +41,33 @@ int fail_cuda(cudaError_t e) {
 }
 
 bool in_open(double v, double lo, double hi) { return v > lo && v < hi && isfinite(v); }
+
+// Host passes over whole fields (checks, conversions, the Ergun mean) in a
+// fixed number of contiguous chunks spread over the host cores: fn(c, lo, hi)
+// handles chunk c = [lo, hi).  The chunking does not depend on the core
+// count, so per-chunk partial results combine identically on any host.
+constexpr int kHostChunks = 64;
+template <typename F>
+void host_chunks(int64_t n, F fn) {
+  const int64_t len = (n + kHostChunks - 1) / kHostChunks;
+  auto run = [&](int first, int stride) {
+    for (int c = first; c < kHostChunks; c += stride) {
+      const int64_t lo = (int64_t)c * len, hi = std::min(n, lo + len);
+      if (lo < hi) fn(c, lo, hi);
+    }
+  };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = n < ((int64_t)1 << 18) ? 1 : (int)std::min<unsigned>(hw ? hw : 1, kHostChunks);
+  if (nt <= 1) {
+    run(0, 1);
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(nt - 1);
+  for (int t = 1; t < nt; ++t) pool.emplace_back(run, t, nt);
+  run(0, nt);
+  for (auto& th : pool) th.join();
+}
 
 }  // namespace
 
@@ -104,10 +133,16 @@ int derive_params(const ltne_params& p, const double* porosity, NodeParams<doubl
       double acc = 0.0;
       const int64_t n = (int64_t)p.nx * p.ny;
       if (porosity) {
-        for (int64_t k = 0; k < n; ++k) {
-          const double ph = porosity[k];
-          acc += ph * ph * ph / ((1 - ph) * (1 - ph));
-        }
+        double part[kHostChunks] = {0};
+        host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
+          double s = 0.0;
+          for (int64_t k = lo; k < hi; ++k) {
+            const double ph = porosity[k];
+            s += ph * ph * ph / ((1 - ph) * (1 - ph));
+          }
+          part[c] = s;
+        });
+        for (int c = 0; c < kHostChunks; ++c) acc += part[c];
         acc /= (double)n;
       } else {
         const double ph = p.porosity;
@@ -349,9 +384,18 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   const ltne_params& p = h->p;
   if ((porosity != nullptr) != (p.porosity_field != 0)) return LTNE_ERR_INVALID_ARG;
   const int64_t n = (int64_t)p.nx * p.ny;
-  if (porosity)
-    for (int64_t k = 0; k < n; ++k)
-      if (!in_open(porosity[k], 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
+  if (porosity) {
+    bool bad[kHostChunks] = {false};
+    host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
+      for (int64_t k = lo; k < hi; ++k)
+        if (!in_open(porosity[k], 0.0, 1.0)) {
+          bad[c] = true;
+          return;
+        }
+    });
+    for (int c = 0; c < kHostChunks; ++c)
+      if (bad[c]) return LTNE_ERR_INVALID_ARG;
+  }
   int rc = derive(h, porosity);
   if (rc != LTNE_OK) return rc;
   drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
@@ -366,11 +410,16 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   const bool dbl = h->ec == 8;
   if (dbl) bd.resize((size_t)n); else bf.resize((size_t)n);
   auto stage = [&](const double* s, double dflt, double ref, char* dst) -> cudaError_t {
-    for (int64_t k = 0; k < n; ++k) {
-      const double v = (s ? s[k] : dflt) - ref;
-      if (!isfinite(v)) return cudaErrorInvalidValue;
-      if (dbl) bd[(size_t)k] = v; else bf[(size_t)k] = (float)v;
-    }
+    bool bad[kHostChunks] = {false};
+    host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
+      for (int64_t k = lo; k < hi; ++k) {
+        const double v = (s ? s[k] : dflt) - ref;
+        if (!isfinite(v)) bad[c] = true;
+        if (dbl) bd[(size_t)k] = v; else bf[(size_t)k] = (float)v;
+      }
+    });
+    for (int c = 0; c < kHostChunks; ++c)
+      if (bad[c]) return cudaErrorInvalidValue;
     const void* hs = dbl ? (const void*)bd.data() : (const void*)bf.data();
     cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->ec, hs, (size_t)p.nx * h->ec,
                                       (size_t)p.nx * h->ec, (size_t)p.ny,
@@ -491,6 +540,19 @@ int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
     return rc;
   }
   layout(h);
+  // Default schedules, the fastest measured on GB300 (8192^2 and 4096^2
+  // cavities): two nodes per thread in 32 x 4 blocks for 16-bit storage
+  // (issue-bound in the one-node form), in 128 x 1 blocks for FP32 (at the
+  // HBM roofline either way), one node per thread for FP64.
+  if (p->storage == LTNE_F16DEV || p->storage == LTNE_BF16DEV) {
+    h->shape.bx = 32;
+    h->shape.by = 4;
+    h->shape.pair = 1;
+  } else if (p->storage == LTNE_F32) {
+    h->shape.bx = 128;
+    h->shape.by = 1;
+    h->shape.pair = 1;
+  }
   *out = h;
   return LTNE_OK;
 }
@@ -577,12 +639,17 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail_cuda(e);
     const double ref = (k == 0) ? 1.0 : (k >= 3 ? p.T_ref : 0.0);  // planes hold deviations
+    double* out = dst[k];
     if (h->ec == 8) {
       const double* t = reinterpret_cast<const double*>(tmp.data());
-      for (int64_t i = 0; i < n; ++i) dst[k][i] = ref + t[i];
+      host_chunks(n, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) out[i] = ref + t[i];
+      });
     } else {
       const float* t = reinterpret_cast<const float*>(tmp.data());
-      for (int64_t i = 0; i < n; ++i) dst[k][i] = ref + (double)t[i];
+      host_chunks(n, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) out[i] = ref + (double)t[i];
+      });
     }
   }
   return LTNE_OK;
@@ -669,6 +736,31 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
 }
 
 int64_t ltne_launch_count(const ltne_handle* h) { return h ? h->launches : 0; }
+
+int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
+                      int32_t nodes_per_thread) {
+  if (!h) return LTNE_ERR_INVALID_ARG;
+  const int64_t threads = (int64_t)block_x * block_y;
+  if (block_x < 32 || block_x > 256 || block_x % 32 != 0 || block_y < 1 || threads > 256)
+    return LTNE_ERR_INVALID_ARG;
+  if (nodes_per_thread != 1 && nodes_per_thread != 2) return LTNE_ERR_INVALID_ARG;
+  if (nodes_per_thread == 2 && (h->p.storage == LTNE_F64 || threads > kPairBlockThreads))
+    return LTNE_ERR_INVALID_ARG;
+  h->shape.bx = block_x;
+  h->shape.by = block_y;
+  h->shape.pair = nodes_per_thread == 2 ? 1 : 0;
+  drop_graphs(h);  // the captured launches carry the old configuration
+  return LTNE_OK;
+}
+
+int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
+                      int32_t* nodes_per_thread) {
+  if (!h || !block_x || !block_y || !nodes_per_thread) return LTNE_ERR_INVALID_ARG;
+  *block_x = h->shape.bx;
+  *block_y = h->shape.by;
+  *nodes_per_thread = h->shape.pair ? 2 : 1;
+  return LTNE_OK;
+}
 
 void ltne_destroy(ltne_handle* h) {
   if (!h) return;

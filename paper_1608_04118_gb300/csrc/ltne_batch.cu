@@ -38,29 +38,58 @@ constexpr int kParamWords = (int)(sizeof(NodeParams<float>) / sizeof(uint32_t));
 static_assert(sizeof(NodeParams<float>) % sizeof(uint32_t) == 0, "NodeParams<float> layout");
 static_assert(kParamWords <= 64, "cavity constants must fit one copy pass of >= 64 threads");
 
+// What a tile needs of its cavity besides the constants.
+struct TileHead {
+  int nx, ny;
+  int64_t pitch, plane, pop_off, mac_off;
+};
+
+__device__ __forceinline__ TileHead tile_head(const BatchCavity* __restrict__ cav, int c) {
+  return TileHead{cav[c].nx, cav[c].ny, cav[c].pitch, cav[c].plane, cav[c].pop_off,
+                  cav[c].mac_off};
+}
+
+// The descriptor, cavity header and constants of a block's next tile are
+// loaded while it works on the current one (constants double-buffered in
+// shared memory), so a tile's population loads start right after the
+// barrier that closes the previous tile.
 __global__ void __launch_bounds__(256) k_batch_step(const float* __restrict__ src,
                                                     float* __restrict__ dst,
                                                     float* __restrict__ mac,
                                                     const BatchCavity* __restrict__ cav,
                                                     const int4* __restrict__ tiles, int ntiles,
                                                     int tx_log2, int write_macros) {
-  __shared__ NodeParams<float> sP;
+  __shared__ NodeParams<float> sP[2];
   const int tid = threadIdx.x;
   const int lx = tid & ((1 << tx_log2) - 1), ly = tid >> tx_log2;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int4 tl = tiles[t];  // (cavity, x0, y0, -)
-    __syncthreads();           // the previous tile is done with sP
-    if (tid < kParamWords)
-      reinterpret_cast<uint32_t*>(&sP)[tid] = reinterpret_cast<const uint32_t*>(&cav[tl.x].P)[tid];
-    __syncthreads();
-    const int nx = cav[tl.x].nx, ny = cav[tl.x].ny;
-    const int x = tl.y + lx, y = tl.z + ly;
-    if (x < nx && y < ny) {
-      const int64_t po = cav[tl.x].pop_off;
-      step_node<float, float, BC_CAVITY>(src + po, dst + po, nullptr, mac + cav[tl.x].mac_off, sP,
-                                         x, y, nx, ny, cav[tl.x].pitch, cav[tl.x].plane, 1.0f,
-                                         1.0f, write_macros, 0u);
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  int4 tl = tiles[t];  // (cavity, x0, y0, -)
+  TileHead hd = tile_head(cav, tl.x);
+  if (tid < kParamWords)
+    reinterpret_cast<uint32_t*>(&sP[0])[tid] = reinterpret_cast<const uint32_t*>(&cav[tl.x].P)[tid];
+  __syncthreads();
+  int buf = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    int4 tl_next = tl;
+    TileHead hd_next = hd;
+    uint32_t word = 0;
+    if (tn < ntiles) {
+      tl_next = tiles[tn];
+      hd_next = tile_head(cav, tl_next.x);
+      if (tid < kParamWords) word = reinterpret_cast<const uint32_t*>(&cav[tl_next.x].P)[tid];
     }
+    const int x = tl.y + lx, y = tl.z + ly;
+    if (x < hd.nx && y < hd.ny)
+      step_node<float, float, BC_CAVITY>(src + hd.pop_off, dst + hd.pop_off, nullptr,
+                                         mac + hd.mac_off, sP[buf], x, y, hd.nx, hd.ny, hd.pitch,
+                                         hd.plane, 1.0f, 1.0f, write_macros, 0u);
+    if (tn < ntiles && tid < kParamWords) reinterpret_cast<uint32_t*>(&sP[buf ^ 1])[tid] = word;
+    __syncthreads();  // sP[buf ^ 1] complete; nobody reads sP[buf] any more
+    buf ^= 1;
+    tl = tl_next;
+    hd = hd_next;
   }
 }
 

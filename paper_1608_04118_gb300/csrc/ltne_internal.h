@@ -32,10 +32,14 @@ struct LatticeArgs {
   void* um_out;             // |u| plane written for the next state
 };
 
-// Launch configuration of the step kernel (chosen by the autotuner).
+// Launch configuration of the step kernel: a block of bx x by threads,
+// each advancing one node or (pair = 1, FP32 arithmetic only, at most
+// kPairBlockThreads threads per block) two neighbouring nodes of a row.
+constexpr int kPairBlockThreads = 128;
 struct StepShape {
   int bx = 128;
   int by = 2;
+  int pair = 0;
 };
 
 // Per-storage-type launchers (one translation unit each).

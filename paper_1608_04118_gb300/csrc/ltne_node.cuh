@@ -481,6 +481,15 @@ template <> struct Codec<__half, float> {
     b = (b + (r & 0x1fffu)) & ~0x1fffu;
     return __float2half_rn(__uint_as_float(b));
   }
+  // Two values at once by the paired conversion with random bits (cvt.rs):
+  // lo takes bits 0-12 of r and goes to the low half, hi bits 16-28 and the
+  // high half -- the rounding of enc() above, value by value, in the normal
+  // FP16 range (below it the random bits sit under the subnormal ulp).
+  static __device__ __forceinline__ uint32_t enc2(float lo, float hi, float scale, uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi * scale), "f"(lo * scale), "r"(r));
+    return d;
+  }
 };
 template <> struct Codec<__nv_bfloat16, float> {
   static constexpr bool kStochastic = true;
@@ -491,6 +500,12 @@ template <> struct Codec<__nv_bfloat16, float> {
   static __device__ __forceinline__ __nv_bfloat16 enc(float v, float, uint32_t r) {
     const uint32_t b = __float_as_uint(v) + (r & 0xffffu);
     return __ushort_as_bfloat16((unsigned short)(b >> 16));
+  }
+  // Two values at once (cvt.rs): lo with bits 0-15 of r, hi with bits 16-31.
+  static __device__ __forceinline__ uint32_t enc2(float lo, float hi, float, uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
   }
 };
 

@@ -46,6 +46,16 @@ __host__ NodeParams<C> cast_params(const NodeParams<double>& d) {
 // Boundary modes (values of LTNE_BC_*).
 constexpr int BC_CAVITY = 0, BC_PERIODIC = 1, BC_CHANNEL = 2;
 
+template <typename S> __device__ __forceinline__ S bits_to(unsigned short b);
+template <> __device__ __forceinline__ __half bits_to<__half>(unsigned short b) {
+  return __ushort_as_half(b);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 bits_to<__nv_bfloat16>(unsigned short b) {
+  return __ushort_as_bfloat16(b);
+}
+template <> __device__ __forceinline__ float bits_to<float>(unsigned short) { return 0.0f; }
+template <> __device__ __forceinline__ double bits_to<double>(unsigned short) { return 0.0; }
+
 template <typename S, typename C>
 struct Pops {
   // Loads the 19 post-collision values streaming into node (x, y):
@@ -83,14 +93,16 @@ struct Pops {
                                                uint32_t seed_step) {
     const uint32_t pl = (uint32_t)plane;
     if constexpr (Codec<S, C>::kStochastic) {
+      // values 2k and 2k + 1 share one random word (low and high half) and
+      // one paired conversion; value 18 takes the low half of the last word
       RandomBits rb(seed_node, seed_step);
-      uint32_t r = 0;
+      auto val = [&](int i) -> C { return i < 9 ? f[i] : (i < 14 ? gf[i - 9] : gs[i - 14]); };
 #pragma unroll
-      for (int i = 0; i < 19; ++i) {
-        if ((i & 1) == 0) r = rb.next();
-        const uint32_t ri = (i & 1) ? (r >> 16) : r;
-        const C v = i < 9 ? f[i] : (i < 14 ? gf[i - 9] : gs[i - 14]);
-        dst[(uint32_t)i * pl + off] = Codec<S, C>::enc(v, scale, ri);
+      for (int i = 0; i < 19; i += 2) {
+        const uint32_t d = Codec<S, C>::enc2(val(i), i + 1 < 19 ? val(i + 1) : C(0), scale,
+                                             rb.next());
+        dst[(uint32_t)i * pl + off] = bits_to<S>((unsigned short)(d & 0xffffu));
+        if (i + 1 < 19) dst[(uint32_t)(i + 1) * pl + off] = bits_to<S>((unsigned short)(d >> 16));
       }
     } else {
 #pragma unroll

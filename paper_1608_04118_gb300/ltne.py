@@ -88,6 +88,9 @@ SIGNATURES = {
     "ltne_get_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "ltne_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "ltne_launch_count": (C.c_int64, [_vp]),
+    "ltne_set_schedule": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+    "ltne_get_schedule": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32)]),
     "ltne_observables_static": (C.c_int, [C.POINTER(ltne_params), _vp, C.c_int64, _vp, C.c_int64,
                                           _vp, C.POINTER(ltne_obs)]),
     "ltne_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_int64, C.c_int32]),
@@ -223,6 +226,18 @@ def ltne_launch_count(h) -> int:
     return int(_lib().ltne_launch_count(h))
 
 
+def ltne_set_schedule(h, block_x, block_y, nodes_per_thread):
+    _check(_lib().ltne_set_schedule(h, int(block_x), int(block_y), int(nodes_per_thread)),
+           "ltne_set_schedule")
+
+
+def ltne_get_schedule(h):
+    bx, by, npt = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib().ltne_get_schedule(h, C.byref(bx), C.byref(by), C.byref(npt)),
+           "ltne_get_schedule")
+    return bx.value, by.value, npt.value
+
+
 def ltne_adjoint_workspace_bytes(h, n_steps, segment) -> int:
     return int(_lib().ltne_adjoint_workspace_bytes(h, int(n_steps), int(segment)))
 
@@ -277,6 +292,11 @@ class Cavity:
     def nodes(self):
         return self.nx * self.ny
 
+    @property
+    def storage(self):
+        """Population storage type: "f64", "f32", "f16" or "bf16"."""
+        return {v: k for k, v in STORAGE.items()}[int(self.params.storage)]
+
     def set_fields(self, porosity=None, rho=None, ux=None, uy=None, T_f=None, T_s=None):
         ltne_set_fields(self.h, self.nodes, porosity, rho, ux, uy, T_f, T_s)
         return self
@@ -301,6 +321,16 @@ class Cavity:
     @property
     def launches(self):
         return ltne_launch_count(self.h)
+
+    def set_schedule(self, block_x, block_y, nodes_per_thread):
+        """Block shape and nodes per thread (1, or 2 in paired FP32) of the
+        step kernel."""
+        ltne_set_schedule(self.h, block_x, block_y, nodes_per_thread)
+        return self
+
+    @property
+    def schedule(self):
+        return ltne_get_schedule(self.h)
 
     def adjoint(self, porosity, n_steps, segment=None, rho=None, T_f=None, T_s=None):
         """Run n_steps from the given initial fields (fluid at rest) and return

@@ -161,3 +161,17 @@ def test_option_validation_without_gpu(lt):
     assert lt.ltne_adjoint_workspace_bytes(h, 100, 10) > 0
     assert lt.ltne_adjoint_workspace_bytes(h, 0, 10) == 0
     lt.ltne_destroy(h)
+    # step schedules: default per storage type; two nodes per thread need
+    # float arithmetic and at most 128 threads per block
+    for storage, default in ((lt.LTNE_F32, (128, 1, 2)), (lt.LTNE_F16DEV, (32, 4, 2)),
+                             (lt.LTNE_BF16DEV, (32, 4, 2)), (lt.LTNE_F64, (128, 2, 1))):
+        h = lt.ltne_create(lt.ltne_default_params(32, 32, storage=storage))
+        assert lt.ltne_get_schedule(h) == default
+        for bad in ((48, 2, 1), (16, 1, 1), (512, 1, 1), (128, 4, 1), (128, 2, 3), (128, 0, 1),
+                    (64, 4, 2), (256, 1, 2)):
+            assert lib.ltne_set_schedule(h, *bad) == lt.LTNE_ERR_INVALID_ARG, bad
+        assert lib.ltne_set_schedule(h, 64, 2, 2) == (
+            lt.LTNE_ERR_INVALID_ARG if storage == lt.LTNE_F64 else lt.LTNE_OK)
+        assert lib.ltne_set_schedule(h, 256, 1, 1) == lt.LTNE_OK
+        assert lt.ltne_get_schedule(h) == (256, 1, 1)
+        lt.ltne_destroy(h)
