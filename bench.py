@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--cavities", type=int, default=256,
                     help="c3: number of cavities (the workload has 256; fewer for profiling)")
     ap.add_argument("--batch-schedule", default="",
-                    help="c3: tile_x,tile_y,blocks instead of the autotuned schedule")
+                    help="c3: tile_x,tile_y,blocks,nodes_per_thread instead of the autotuned "
+                         "schedule")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -313,7 +314,9 @@ def run_batch(args):
             "config": {"workload": "%d porous LTNE cavities, sides 64..512, aspect 1-2, "
                                    "seed 3" % len(cavs), "nodes": nodes,
                        "schedule": {"tile_x": sched[0], "tile_y": sched[1],
-                                    "blocks": sched[2], "tuning_s": tune_s,
+                                    "blocks": sched[2],
+                                    "nodes_per_thread": sched[3] if len(sched) > 3 else 1,
+                                    "tuning_s": tune_s,
                                     "trials": len(table)}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": kind, "bytes_per_lup": 152},
@@ -371,7 +374,9 @@ def run_reduced(args):
     ref, robs = o.macros(), o.observables()
     errors = {}
     for st in ("f32", "f16", "bf16"):
-        cav = Cavity(m, m, stream=stream, storage=st, **phys).set_fields().step(c["steps"])
+        # the schedule the MLUPS above were measured with
+        cav = Cavity(m, m, stream=stream, storage=st, **phys)
+        cav.set_schedule(*schedules[(st, False)]).set_fields().step(c["steps"])
         got, gobs = cav.fields(), cav.observables()
         e = {}
         un = np.linalg.norm(np.stack([ref["ux"], ref["uy"]]))
@@ -444,6 +449,34 @@ def run_adjoint(args):
     torch.cuda.synchronize()
     t_fwd = ev0.elapsed_time(ev1) / 1e3
     nodes = nx * ny
+
+    # context: the same physics on a 1024^2 lattice (1000 steps), where a
+    # step is several waves of blocks rather than one latency-bound wave
+    def at_size(n, k):
+        ph = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+        cv = Cavity(n, n, stream=stream, storage="f32", permeability=LTNE_K_ERGUN,
+                    porosity_field=1, **kw)
+        sg = int(math.ceil(math.sqrt(k)))
+        cv.adjoint(ph, 2 * sg, segment=sg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cv.adjoint(ph, k, segment=sg)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t0
+        cv.set_fields(porosity=ph)
+        with torch.cuda.stream(stream):
+            cv.step(20)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cv.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tf = e0.elapsed_time(e1) / 1e3
+        cv.close()
+        return {"n": n, "steps": k, "segment": sg, "mlups": n * n * k / ta / 1e6,
+                "plain_forward_mlups": n * n * k / tf / 1e6, "ratio_to_plain_forward": tf / ta}
+
+    big = at_size(1024, 1000)
     line = {"metric": "MLUPS (forward + adjoint, 256x256)", "value": nodes * steps / t_adj / 1e6,
             "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -453,7 +486,8 @@ def run_adjoint(args):
                        "objective": "(Nu_f,hot + Nu_s,hot)/2 at the last step"},
             "seconds": t_adj, "plain_forward_mlups": nodes * steps / t_fwd / 1e6,
             "ratio_to_plain_forward": (nodes * steps / t_adj) / (nodes * steps / t_fwd),
-            "J": J, "dJ_dH": dH, "max_abs_dJ_dphi": float(g.abs().max())}
+            "J": J, "dJ_dH": dH, "max_abs_dJ_dphi": float(g.abs().max()),
+            "same_physics_1024": big}
     print(json.dumps(line), flush=True)
 
 
@@ -534,6 +568,20 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = BYTES_PER_LUP[args.storage] * nodes / per_launch / 1e9
     ob = cav.observables()
+    # the FP64 observables reduction (one ltne_observables call: two kernels,
+    # the 18-value readback and the host finish), median of 5
+    obs_t = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cav.observables()
+        e1.record(stream)
+        e1.synchronize()
+        obs_t.append(e0.elapsed_time(e1) / 1e3)
+    obs_s = sorted(obs_t)[2]
+    esz = 8 if args.storage == "f64" else 4
+    obs_bytes = (5 + 1 + 4 + 4) * esz * nodes  # macros, porosity, snapshot read + write
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -587,6 +635,9 @@ def main():
                      "kernel": "%s<%s> (one launch = one step of %d nodes)"
                                % ("k_step_pair" if schedule[2] == 2 else "k_step", args.storage,
                                   nodes)},
+        "observables_reduction": {"ms": obs_s * 1e3, "bytes_per_node": obs_bytes // nodes,
+                                  "achieved_GBps": obs_bytes / obs_s / 1e9,
+                                  "frac_of_peak": obs_bytes / obs_s / 1e9 / peak},
         "gpu_launches": int(launches),
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "observables": {"Nu_f_hot": ob["Nu_f_hot"], "Nu_s_hot": ob["Nu_s_hot"],

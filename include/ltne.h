@@ -206,9 +206,10 @@ int64_t ltne_launch_count(const ltne_handle* h);
    row in paired FP32 arithmetic (FP32, FP16 and BF16 storage only, and
    block_x * block_y <= 128).  The schedule changes no result beyond FP32
    rounding: the arithmetic per node is the same, and for a given
-   nodes_per_thread the block shape changes no bit.  Defaults: 32 x 4 with
-   two nodes per thread (FP16, BF16), 128 x 1 with two (FP32), 128 x 2 with
-   one (FP64).  May be called at any time between steps.
+   nodes_per_thread the block shape changes no bit.  Defaults, for lattices
+   of 2^20 nodes or more: 32 x 4 with two nodes per thread (FP16, BF16),
+   128 x 1 with two (FP32), 128 x 2 with one (FP64); smaller lattices:
+   128 x 2 with one.  May be called at any time between steps.
    LTNE_ERR_INVALID_ARG for other schedules. */
 int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
                       int32_t nodes_per_thread);
@@ -310,10 +311,16 @@ int64_t ltne_batch_nodes(const ltne_batch* b);
    block per tile). */
 int ltne_batch_bind_workspace(ltne_batch* b, void* device_ptr, size_t bytes);
 
-/* Launch schedule: tiles of tile_x x tile_y nodes (tile_x in 32..256 and
-   tile_y in 1..8, powers of two, 64 <= tile_x*tile_y <= 256; one thread per
-   node) walked by `blocks` persistent blocks (0: one block per tile). */
-int ltne_batch_set_schedule(ltne_batch* b, int32_t tile_x, int32_t tile_y, int32_t blocks);
+/* Launch schedule: tiles of tile_x x tile_y nodes walked by `blocks`
+   persistent blocks (0: one block per tile), each thread advancing
+   nodes_per_thread = 1 node or 2 neighbouring nodes of a row (paired FP32
+   arithmetic).  A block has tile_x / nodes_per_thread x tile_y threads:
+   tile_x / nodes_per_thread in 32..256 and tile_y in 1..8, powers of two,
+   64 to 256 threads per block (64 to 128 with two nodes per thread).
+   Results do not depend on the schedule beyond FP32 contraction order
+   (bitwise for a fixed nodes_per_thread). */
+int ltne_batch_set_schedule(ltne_batch* b, int32_t tile_x, int32_t tile_y, int32_t blocks,
+                            int32_t nodes_per_thread);
 
 /* Every cavity at rest: rho = 1, u = 0, T_f = T_s = its T_ref (equilibrium
    populations, walls included).  Resets the step counter. */

@@ -1,20 +1,23 @@
 """Launch-schedule autotuner for the batched form.
 
-Times candidate schedules (tile shape x persistent grid size) of a
-``Batch`` with CUDA events on its stream and keeps the fastest.  Candidate
-grid sizes are multiples of the SM count; 0 means one block per tile.
+Times candidate schedules (tile shape x persistent grid size x nodes per
+thread) of a ``Batch`` with CUDA events on its stream and keeps the
+fastest.  Candidate grid sizes are multiples of the SM count; 0 means one
+block per tile.
 """
 from __future__ import annotations
 
 import itertools
 
-TILE_SHAPES = ((32, 4), (64, 2), (64, 4), (128, 1), (128, 2), (256, 1))
+# (tile_x, tile_y, nodes per thread): tiles in nodes, tile_x / npt threads across
+TILE_SHAPES = ((32, 4, 1), (64, 2, 1), (64, 4, 1), (128, 1, 1), (128, 2, 1), (256, 1, 1),
+               (64, 2, 2), (64, 4, 2), (128, 1, 2), (128, 2, 2), (256, 1, 2))
 BLOCKS_PER_SM = (2, 4, 8, 16)
 
 
 def candidates(sm_count):
-    for (tx, ty), k in itertools.product(TILE_SHAPES, BLOCKS_PER_SM + (0,)):
-        yield tx, ty, (k * sm_count if k else 0)
+    for (tx, ty, npt), k in itertools.product(TILE_SHAPES, BLOCKS_PER_SM + (0,)):
+        yield tx, ty, (k * sm_count if k else 0), npt
 
 
 def time_schedule(batch, schedule, steps, warmup=2):

@@ -27,6 +27,7 @@
 
 #include "ltne.h"
 #include "ltne_internal.h"
+#include "ltne_handle.h"
 #include "ltne_step_impl.cuh"
 #include "ltne_adjoint.cuh"
 

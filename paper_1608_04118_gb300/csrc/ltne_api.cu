@@ -12,6 +12,7 @@
 
 #include "ltne.h"
 #include "ltne_internal.h"
+#include "ltne_handle.h"
 
 using namespace ltne;
 
@@ -67,6 +68,95 @@ void host_chunks(int64_t n, F fn) {
   for (int t = 1; t < nt; ++t) pool.emplace_back(run, t, nt);
   run(0, nt);
   for (auto& th : pool) th.join();
+}
+
+// Pinned staging of whole fields between host arrays and the device planes:
+// rows go in blocks through two pinned buffers, so that converting one block
+// on the host overlaps the copy of the other.
+constexpr size_t kPinBytes = (size_t)32 << 20;
+
+void release_pinned(ltne_handle* h) {
+  for (int k = 0; k < 2; ++k) {
+    if (h->pin[k]) cudaFreeHost(h->pin[k]);
+    if (h->pin_ev[k]) cudaEventDestroy(h->pin_ev[k]);
+    h->pin[k] = nullptr;
+    h->pin_ev[k] = nullptr;
+  }
+  h->pin_bytes = 0;
+}
+
+cudaError_t ensure_pinned(ltne_handle* h, size_t row_bytes) {
+  const size_t bytes = std::max(row_bytes, kPinBytes);
+  if (h->pin_bytes >= bytes) return cudaSuccess;
+  release_pinned(h);
+  for (int k = 0; k < 2; ++k) {
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&h->pin[k]), bytes,
+                                  cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->pin_ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      release_pinned(h);
+      return e;
+    }
+  }
+  h->pin_bytes = bytes;
+  return cudaSuccess;
+}
+
+// Host -> device: fill(buf, y0, y1) writes rows [y0, y1) of the field,
+// packed (nx values of ec bytes per row), into a pinned buffer and returns
+// false on a value it rejects; each block is then copied into the device
+// plane at dev (row pitch h->pitch).  Asynchronous on the handle's stream.
+template <typename Fill>
+int upload_field(ltne_handle* h, char* dev, Fill fill) {
+  const int nx = h->p.nx, ny = h->p.ny;
+  const size_t row = (size_t)nx * h->ec, dpitch = (size_t)h->pitch * h->ec;
+  cudaError_t e = ensure_pinned(h, row);
+  if (e != cudaSuccess) return fail_cuda(e);
+  const int rows = (int)std::max<size_t>(1, h->pin_bytes / row);
+  int slot = 0;
+  for (int y0 = 0; y0 < ny; y0 += rows, slot ^= 1) {
+    const int y1 = std::min(ny, y0 + rows);
+    e = cudaEventSynchronize(h->pin_ev[slot]);  // its previous copy is done
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (!fill(h->pin[slot], y0, y1)) {
+      cudaStreamSynchronize(h->stream);
+      return LTNE_ERR_INVALID_ARG;
+    }
+    e = cudaMemcpy2DAsync(dev + (size_t)y0 * dpitch, dpitch, h->pin[slot], row, row,
+                          (size_t)(y1 - y0), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->pin_ev[slot], h->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  return LTNE_OK;
+}
+
+// Device -> host: blocks of rows of the plane at dev are copied into the
+// pinned buffers in turn, and drain(buf, y0, y1) converts each block while
+// the next one is in flight.  Returns when the whole field is drained.
+template <typename Drain>
+int download_field(ltne_handle* h, const char* dev, Drain drain) {
+  const int nx = h->p.nx, ny = h->p.ny;
+  const size_t row = (size_t)nx * h->ec, dpitch = (size_t)h->pitch * h->ec;
+  cudaError_t e = ensure_pinned(h, row);
+  if (e != cudaSuccess) return fail_cuda(e);
+  const int rows = (int)std::max<size_t>(1, h->pin_bytes / row);
+  const int nb = (ny + rows - 1) / rows;
+  for (int b = 0; b <= nb; ++b) {
+    if (b < nb) {
+      const int y0 = b * rows, y1 = std::min(ny, y0 + rows);
+      e = cudaMemcpy2DAsync(h->pin[b & 1], row, dev + (size_t)y0 * dpitch, dpitch, row,
+                            (size_t)(y1 - y0), cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(h->pin_ev[b & 1], h->stream);
+      if (e != cudaSuccess) return fail_cuda(e);
+    }
+    if (b > 0) {
+      const int y0 = (b - 1) * rows, y1 = std::min(ny, y0 + rows);
+      e = cudaEventSynchronize(h->pin_ev[(b - 1) & 1]);
+      if (e != cudaSuccess) return fail_cuda(e);
+      drain(h->pin[(b - 1) & 1], y0, y1);
+    }
+  }
+  return LTNE_OK;
 }
 
 }  // namespace
@@ -405,37 +495,34 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   const double defaults[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
   const double refs[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
   const double* src[5] = {rho, ux, uy, T_f, T_s};
-  std::vector<double> bd;
-  std::vector<float> bf;
   const bool dbl = h->ec == 8;
-  if (dbl) bd.resize((size_t)n); else bf.resize((size_t)n);
-  auto stage = [&](const double* s, double dflt, double ref, char* dst) -> cudaError_t {
-    bool bad[kHostChunks] = {false};
-    host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
-      for (int64_t k = lo; k < hi; ++k) {
-        const double v = (s ? s[k] : dflt) - ref;
-        if (!isfinite(v)) bad[c] = true;
-        if (dbl) bd[(size_t)k] = v; else bf[(size_t)k] = (float)v;
-      }
+  const int nx = p.nx;
+  // one field, rows [y0, y1), as deviations in the compute type; false if
+  // any value is not finite
+  auto stage = [&](const double* s, double dflt, double ref, char* dst) -> int {
+    return upload_field(h, dst, [&](char* buf, int y0, int y1) {
+      const int64_t base = (int64_t)y0 * nx, cnt = (int64_t)(y1 - y0) * nx;
+      bool bad[kHostChunks] = {false};
+      host_chunks(cnt, [&](int c, int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi; ++k) {
+          const double v = (s ? s[base + k] : dflt) - ref;
+          if (!isfinite(v)) bad[c] = true;
+          if (dbl) reinterpret_cast<double*>(buf)[k] = v;
+          else reinterpret_cast<float*>(buf)[k] = (float)v;
+        }
+      });
+      for (int c = 0; c < kHostChunks; ++c)
+        if (bad[c]) return false;
+      return true;
     });
-    for (int c = 0; c < kHostChunks; ++c)
-      if (bad[c]) return cudaErrorInvalidValue;
-    const void* hs = dbl ? (const void*)bd.data() : (const void*)bf.data();
-    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->ec, hs, (size_t)p.nx * h->ec,
-                                      (size_t)p.nx * h->ec, (size_t)p.ny,
-                                      cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(h->stream);  // the staging buffer is reused
   };
   for (int k = 0; k < 5; ++k) {
-    cudaError_t e = stage(src[k], defaults[k], refs[k],
-                          h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
-    if (e == cudaErrorInvalidValue) return LTNE_ERR_INVALID_ARG;
-    if (e != cudaSuccess) return fail_cuda(e);
+    rc = stage(src[k], defaults[k], refs[k], h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
+    if (rc != LTNE_OK) return rc;
   }
   if (porosity) {
-    cudaError_t e = stage(porosity, 0.0, 0.0, h->ws + h->off_phi);
-    if (e != cudaSuccess) return fail_cuda(e);
+    rc = stage(porosity, 0.0, 0.0, h->ws + h->off_phi);
+    if (rc != LTNE_OK) return rc;
   }
   // Zero both population buffers (row padding included, so that state
   // blobs are deterministic) and the residual snapshot.
@@ -540,11 +627,17 @@ int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
     return rc;
   }
   layout(h);
-  // Default schedules, the fastest measured on GB300 (8192^2 and 4096^2
-  // cavities): two nodes per thread in 32 x 4 blocks for 16-bit storage
-  // (issue-bound in the one-node form), in 128 x 1 blocks for FP32 (at the
-  // HBM roofline either way), one node per thread for FP64.
-  if (p->storage == LTNE_F16DEV || p->storage == LTNE_BF16DEV) {
+  // Default schedules, the fastest measured on GB300: from 2^20 nodes up,
+  // two nodes per thread in 32 x 4 blocks for 16-bit storage (issue-bound
+  // in the one-node form) and in 128 x 1 blocks for FP32 (at the HBM
+  // roofline either way); one node per thread in 128 x 2 blocks for FP64
+  // and for smaller lattices, whose steps are a single wave bound by the
+  // latency of one thread's work (the 256 cavities of 64..512 nodes a side
+  // ran one by one at 32.2 GLUPS with one node per thread, 23.4 with two).
+  const bool large = (int64_t)p->nx * p->ny >= ((int64_t)1 << 20);
+  if (!large) {
+    // 128 x 2, one node per thread
+  } else if (p->storage == LTNE_F16DEV || p->storage == LTNE_BF16DEV) {
     h->shape.bx = 32;
     h->shape.by = 4;
     h->shape.pair = 1;
@@ -626,31 +719,28 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
   if (!h) return LTNE_ERR_INVALID_ARG;
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;
-  const int64_t n = (int64_t)p.nx * p.ny;
   double* dst[5] = {rho, ux, uy, T_f, T_s};
-  std::vector<char> tmp((size_t)n * h->ec);
+  const int nx = p.nx;
   for (int k = 0; k < 5; ++k) {
     if (!dst[k]) continue;
-    cudaError_t e = cudaMemcpy2DAsync(tmp.data(), (size_t)p.nx * h->ec,
-                                      h->ws + h->off_mac + (size_t)k * h->plane * h->ec,
-                                      (size_t)h->pitch * h->ec, (size_t)p.nx * h->ec,
-                                      (size_t)p.ny, cudaMemcpyDeviceToHost, h->stream);
-    if (e != cudaSuccess) return fail_cuda(e);
-    e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return fail_cuda(e);
     const double ref = (k == 0) ? 1.0 : (k >= 3 ? p.T_ref : 0.0);  // planes hold deviations
     double* out = dst[k];
-    if (h->ec == 8) {
-      const double* t = reinterpret_cast<const double*>(tmp.data());
-      host_chunks(n, [&](int, int64_t lo, int64_t hi) {
-        for (int64_t i = lo; i < hi; ++i) out[i] = ref + t[i];
-      });
-    } else {
-      const float* t = reinterpret_cast<const float*>(tmp.data());
-      host_chunks(n, [&](int, int64_t lo, int64_t hi) {
-        for (int64_t i = lo; i < hi; ++i) out[i] = ref + (double)t[i];
-      });
-    }
+    const int rc = download_field(
+        h, h->ws + h->off_mac + (size_t)k * h->plane * h->ec, [&](const char* buf, int y0, int y1) {
+          const int64_t base = (int64_t)y0 * nx, cnt = (int64_t)(y1 - y0) * nx;
+          if (h->ec == 8) {
+            const double* t = reinterpret_cast<const double*>(buf);
+            host_chunks(cnt, [&](int, int64_t lo, int64_t hi) {
+              for (int64_t i = lo; i < hi; ++i) out[base + i] = ref + t[i];
+            });
+          } else {
+            const float* t = reinterpret_cast<const float*>(buf);
+            host_chunks(cnt, [&](int, int64_t lo, int64_t hi) {
+              for (int64_t i = lo; i < hi; ++i) out[base + i] = ref + (double)t[i];
+            });
+          }
+        });
+    if (rc != LTNE_OK) return rc;
   }
   return LTNE_OK;
 }
@@ -765,6 +855,7 @@ int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
 void ltne_destroy(ltne_handle* h) {
   if (!h) return;
   drop_graphs(h);
+  release_pinned(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }

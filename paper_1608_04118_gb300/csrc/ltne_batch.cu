@@ -6,10 +6,12 @@
 //
 // Work decomposition: every cavity is cut into tiles of TX x TY nodes; the
 // tile list (cavity, x0, y0) is built on the host for the schedule the
-// autotuner picked.  A block of TX*TY threads walks the list with a stride of
-// the grid size (round-robin, so block loads differ by at most one tile),
-// stages the tile's cavity constants in shared memory and updates one node
-// per thread.  FP32 storage and arithmetic, uniform porosity per cavity.
+// autotuner picked.  A block of TX*TY/NPT threads walks the list with a
+// stride of the grid size (round-robin, so block loads differ by at most one
+// tile), stages the tile's cavity constants in shared memory and updates
+// NPT = 1 node per thread, or NPT = 2 neighbouring nodes in paired FP32
+// arithmetic (the two-node step of ltne_pair.cuh).  FP32 storage and
+// arithmetic, uniform porosity per cavity.
 #include <math.h>
 #include <string.h>
 
@@ -17,7 +19,7 @@
 
 #include "ltne.h"
 #include "ltne_internal.h"
-#include "ltne_step_impl.cuh"
+#include "ltne_pair.cuh"
 
 using namespace ltne;
 
@@ -25,18 +27,30 @@ namespace {
 
 constexpr int kGraphSteps = 32;
 
+// A cavity's constants for the one-node step (P) and, lane-broadcast, for
+// the two-node step (P2).
+struct BatchConst {
+  NodeParams<float> P;
+  NodeParams<F2> P2;
+};
+
 struct BatchCavity {
   int32_t nx, ny;
   int64_t pitch, plane;
   int64_t pop_off;  // element offset of the cavity's 19 planes in either buffer
   int64_t mac_off;  // element offset of its 5 macro planes
   int64_t prev_off; // element offset of its 4 residual snapshot planes
-  NodeParams<float> P;
+  BatchConst K;
 };
 
-constexpr int kParamWords = (int)(sizeof(NodeParams<float>) / sizeof(uint32_t));
 static_assert(sizeof(NodeParams<float>) % sizeof(uint32_t) == 0, "NodeParams<float> layout");
-static_assert(kParamWords <= 64, "cavity constants must fit one copy pass of >= 64 threads");
+static_assert(sizeof(BatchConst) % sizeof(uint32_t) == 0, "BatchConst layout");
+// Words of constants staged per tile: the one-node step reads P only.
+template <int NPT>
+constexpr int const_words() {
+  return (int)((NPT == 1 ? sizeof(NodeParams<float>) : sizeof(BatchConst)) / sizeof(uint32_t));
+}
+constexpr int kMinBlockThreads = 64;  // every schedule has at least this many
 
 // What a tile needs of its cavity besides the constants.
 struct TileHead {
@@ -53,40 +67,75 @@ __device__ __forceinline__ TileHead tile_head(const BatchCavity* __restrict__ ca
 // loaded while it works on the current one (constants double-buffered in
 // shared memory), so a tile's population loads start right after the
 // barrier that closes the previous tile.
-__global__ void __launch_bounds__(256) k_batch_step(const float* __restrict__ src,
-                                                    float* __restrict__ dst,
-                                                    float* __restrict__ mac,
-                                                    const BatchCavity* __restrict__ cav,
-                                                    const int4* __restrict__ tiles, int ntiles,
-                                                    int tx_log2, int write_macros) {
-  __shared__ NodeParams<float> sP[2];
-  const int tid = threadIdx.x;
+// Register budgets: 64 per thread for the one-node step (it fits without
+// spilling; left free, the tile pipeline takes 124), the pair kernel's for two.
+template <int NPT>
+__global__ void __launch_bounds__(NPT == 1 ? 256 : kPairMaxThreads, NPT == 1 ? 4 : kPairMinBlocks)
+    k_batch_step(const float* __restrict__ src, float* __restrict__ dst, float* __restrict__ mac,
+                 const BatchCavity* __restrict__ cav, const int4* __restrict__ tiles, int ntiles,
+                 int tx_log2, int write_macros) {
+  constexpr int kWords = const_words<NPT>();
+  constexpr int kPer = (kWords + kMinBlockThreads - 1) / kMinBlockThreads;
+  __shared__ BatchConst sK[2];
+  const int tid = threadIdx.x, nthreads = blockDim.x;
   const int lx = tid & ((1 << tx_log2) - 1), ly = tid >> tx_log2;
+  auto words = [&](int c) { return reinterpret_cast<const uint32_t*>(&cav[c].K); };
   int t = blockIdx.x;
   if (t >= ntiles) return;
   int4 tl = tiles[t];  // (cavity, x0, y0, -)
   TileHead hd = tile_head(cav, tl.x);
-  if (tid < kParamWords)
-    reinterpret_cast<uint32_t*>(&sP[0])[tid] = reinterpret_cast<const uint32_t*>(&cav[tl.x].P)[tid];
+  for (int w = tid; w < kWords; w += nthreads)
+    reinterpret_cast<uint32_t*>(&sK[0])[w] = words(tl.x)[w];
   __syncthreads();
   int buf = 0;
   for (; t < ntiles; t += gridDim.x) {
     const int tn = t + gridDim.x;
     int4 tl_next = tl;
     TileHead hd_next = hd;
-    uint32_t word = 0;
+    uint32_t word[kPer];
     if (tn < ntiles) {
       tl_next = tiles[tn];
       hd_next = tile_head(cav, tl_next.x);
-      if (tid < kParamWords) word = reinterpret_cast<const uint32_t*>(&cav[tl_next.x].P)[tid];
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int w = tid + k * nthreads;
+        word[k] = w < kWords ? words(tl_next.x)[w] : 0u;
+      }
     }
-    const int x = tl.y + lx, y = tl.z + ly;
-    if (x < hd.nx && y < hd.ny)
-      step_node<float, float, BC_CAVITY>(src + hd.pop_off, dst + hd.pop_off, nullptr,
-                                         mac + hd.mac_off, sP[buf], x, y, hd.nx, hd.ny, hd.pitch,
-                                         hd.plane, 1.0f, 1.0f, write_macros, 0u);
-    if (tn < ntiles && tid < kParamWords) reinterpret_cast<uint32_t*>(&sP[buf ^ 1])[tid] = word;
-    __syncthreads();  // sP[buf ^ 1] complete; nobody reads sP[buf] any more
+    const float* s = src + hd.pop_off;
+    float* d = dst + hd.pop_off;
+    float* m = mac + hd.mac_off;
+    const int y = tl.z + ly;
+    if constexpr (NPT == 1) {
+      const int x = tl.y + lx;
+      if (x < hd.nx && y < hd.ny)
+        step_node<float, float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P, x, y, hd.nx, hd.ny,
+                                           hd.pitch, hd.plane, 1.0f, 1.0f, write_macros, 0u);
+    } else {
+      const int x0 = tl.y + 2 * lx;
+      if (x0 < hd.nx && y < hd.ny) {
+        if (x0 > 0 && x0 + 2 < hd.nx) {
+          step_pair<float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P2, x0, y, hd.nx, hd.ny,
+                                      (uint32_t)hd.pitch, (uint32_t)hd.plane, 1.0f, 1.0f,
+                                      write_macros, 0u, nullptr, nullptr);
+        } else {  // a wall node in the pair, or the last node of an odd row
+          step_node<float, float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P, x0, y, hd.nx, hd.ny,
+                                             hd.pitch, hd.plane, 1.0f, 1.0f, write_macros, 0u);
+          if (x0 + 1 < hd.nx)
+            step_node<float, float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P, x0 + 1, y, hd.nx,
+                                               hd.ny, hd.pitch, hd.plane, 1.0f, 1.0f,
+                                               write_macros, 0u);
+        }
+      }
+    }
+    if (tn < ntiles) {
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int w = tid + k * nthreads;
+        if (w < kWords) reinterpret_cast<uint32_t*>(&sK[buf ^ 1])[w] = word[k];
+      }
+    }
+    __syncthreads();  // sK[buf ^ 1] complete; nobody reads sK[buf] any more
     buf ^= 1;
     tl = tl_next;
     hd = hd_next;
@@ -118,7 +167,7 @@ struct ltne_batch {
          off_tiles = 0, ws_bytes = 0;
   char* ws = nullptr;
   // schedule
-  int tx = 128, ty = 2, blocks = 0;
+  int tx = 128, ty = 2, blocks = 0, npt = 1;
   int64_t ntiles = 0;
   bool schedule_uploaded = false;
   // state
@@ -136,10 +185,16 @@ int64_t count_tiles(const ltne_batch* b, int tx, int ty) {
   return n;
 }
 
-bool valid_shape(int tx, int ty) {
-  if (tx < 32 || tx > 256 || (tx & (tx - 1)) != 0) return false;
+// Tiles of tx x ty nodes, npt nodes per thread: tx / npt threads across
+// (32..256, a power of two), ty in 1..8 (a power of two), 64 to 256 threads
+// per block (64 to 128 with two nodes per thread).
+bool valid_shape(int tx, int ty, int npt) {
+  if (npt != 1 && npt != 2) return false;
+  const int txt = tx / npt;
+  if (tx % npt != 0 || txt < 32 || txt > 256 || (txt & (txt - 1)) != 0) return false;
   if (ty < 1 || ty > 8 || (ty & (ty - 1)) != 0) return false;
-  return tx * ty >= 64 && tx * ty <= 256;
+  const int threads = txt * ty;
+  return threads >= kMinBlockThreads && threads <= (npt == 1 ? 256 : kPairMaxThreads);
 }
 
 void drop_graphs(ltne_batch* b) {
@@ -168,17 +223,23 @@ int upload_schedule(ltne_batch* b) {
 }
 
 cudaError_t launch_batch_step(ltne_batch* b, int src_buf, int write_macros, cudaStream_t st) {
-  const int threads = b->tx * b->ty;
+  const int txt = b->tx / b->npt;  // threads across a tile
+  const int threads = txt * b->ty;
   const int64_t grid64 = b->blocks > 0 ? (int64_t)b->blocks : b->ntiles;
   const int grid = (int)(grid64 < 1 ? 1 : (grid64 > (1 << 30) ? (1 << 30) : grid64));
   int tx_log2 = 0;
-  while ((1 << tx_log2) < b->tx) ++tx_log2;
-  k_batch_step<<<grid, threads, 0, st>>>(
-      reinterpret_cast<const float*>(b->ws + b->off_pop[src_buf]),
-      reinterpret_cast<float*>(b->ws + b->off_pop[src_buf ^ 1]),
-      reinterpret_cast<float*>(b->ws + b->off_mac),
-      reinterpret_cast<const BatchCavity*>(b->ws + b->off_cav),
-      reinterpret_cast<const int4*>(b->ws + b->off_tiles), (int)b->ntiles, tx_log2, write_macros);
+  while ((1 << tx_log2) < txt) ++tx_log2;
+  const float* src = reinterpret_cast<const float*>(b->ws + b->off_pop[src_buf]);
+  float* dst = reinterpret_cast<float*>(b->ws + b->off_pop[src_buf ^ 1]);
+  float* mac = reinterpret_cast<float*>(b->ws + b->off_mac);
+  const BatchCavity* cav = reinterpret_cast<const BatchCavity*>(b->ws + b->off_cav);
+  const int4* tiles = reinterpret_cast<const int4*>(b->ws + b->off_tiles);
+  if (b->npt == 2)
+    k_batch_step<2><<<grid, threads, 0, st>>>(src, dst, mac, cav, tiles, (int)b->ntiles, tx_log2,
+                                              write_macros);
+  else
+    k_batch_step<1><<<grid, threads, 0, st>>>(src, dst, mac, cav, tiles, (int)b->ntiles, tx_log2,
+                                              write_macros);
   return cudaGetLastError();
 }
 
@@ -245,7 +306,8 @@ int ltne_batch_create(const ltne_params* params, int32_t count, void* cuda_strea
     cv.pop_off = pop;
     cv.mac_off = mac;
     cv.prev_off = prev;
-    cv.P = cast_params<float>(b->Pd[c]);
+    cv.K.P = cast_params<float>(b->Pd[c]);
+    cv.K.P2 = cast_params<F2>(b->Pd[c]);
     pop += 19 * cv.plane;
     mac += 5 * cv.plane;
     prev += 4 * cv.plane;
@@ -257,12 +319,13 @@ int ltne_batch_create(const ltne_params* params, int32_t count, void* cuda_strea
   b->mac_elems = mac;
   b->prev_elems = prev;
   // capacity of the tile list: the largest count over every allowed shape
-  for (int tx = 32; tx <= 256; tx *= 2)
-    for (int ty = 1; ty <= 8; ty *= 2)
-      if (valid_shape(tx, ty)) {
-        const int64_t t = count_tiles(b, tx, ty);
-        if (t > b->max_tiles) b->max_tiles = t;
-      }
+  for (int npt = 1; npt <= 2; ++npt)
+    for (int tx = 32; tx <= 512; tx *= 2)
+      for (int ty = 1; ty <= 8; ty *= 2)
+        if (valid_shape(tx, ty, npt)) {
+          const int64_t t = count_tiles(b, tx, ty);
+          if (t > b->max_tiles) b->max_tiles = t;
+        }
   const size_t A = 256;
   size_t off = 0;
   for (int k = 0; k < 2; ++k) {
@@ -306,12 +369,15 @@ int ltne_batch_bind_workspace(ltne_batch* b, void* device_ptr, size_t bytes) {
   return upload_schedule(b);
 }
 
-int ltne_batch_set_schedule(ltne_batch* b, int32_t tile_x, int32_t tile_y, int32_t blocks) {
-  if (!b || !valid_shape(tile_x, tile_y) || blocks < 0) return LTNE_ERR_INVALID_ARG;
+int ltne_batch_set_schedule(ltne_batch* b, int32_t tile_x, int32_t tile_y, int32_t blocks,
+                            int32_t nodes_per_thread) {
+  if (!b || !valid_shape(tile_x, tile_y, nodes_per_thread) || blocks < 0)
+    return LTNE_ERR_INVALID_ARG;
   if (!b->ws) return LTNE_ERR_STATE;
   b->tx = tile_x;
   b->ty = tile_y;
   b->blocks = blocks;
+  b->npt = nodes_per_thread;
   return upload_schedule(b);
 }
 

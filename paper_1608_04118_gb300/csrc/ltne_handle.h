@@ -1,0 +1,48 @@
+// ltne_handle.h -- host state of one lattice handle (opaque to C callers),
+// shared by the translation units that implement the ltne_* entry points.
+// Kept apart from ltne_internal.h, which holds what the kernels see.
+#pragma once
+
+#include "ltne_internal.h"
+
+// Host state of one lattice (opaque to C callers).
+struct ltne_handle {
+  ltne_params p;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  ltne::NodeParams<double> P{};
+  ltne::StepShape shape;
+  // derived lattice values
+  double L = 0, nu_f = 0, alpha_f = 0, d_ergun = 0;
+  // layout
+  int64_t pitch = 0, plane = 0;
+  size_t es = 0, ec = 0;  // storage / compute element sizes
+  size_t off_pop[2] = {0, 0}, off_phi = 0, off_mac = 0, off_prev = 0, off_part = 0, off_out = 0;
+  size_t off_tick = 0;
+  size_t off_um[2] = {0, 0};  // |u| planes (local h_v of Eq. 52)
+  size_t ws_bytes = 0;
+  char* ws = nullptr;
+  int red_blocks = 1;
+  // state
+  int cur = 0;
+  int64_t step = 0;
+  bool fields_set = false;
+  bool have_prev = false;
+  float enc_scale = 1.0f;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t launches = 0;
+  // two pinned host buffers that stage whole fields in and out (allocated
+  // at the first set_fields / get_fields, freed by ltne_destroy)
+  char* pin[2] = {nullptr, nullptr};
+  cudaEvent_t pin_ev[2] = {nullptr, nullptr};
+  size_t pin_bytes = 0;
+};
+
+namespace ltne {
+// Initial state S_0 from host fields (ltne_set_fields); pre_out, if not
+// null, also receives S_0 (compute type, population-plane layout).
+int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, const double* ux,
+                    const double* uy, const double* T_f, const double* T_s, void* pre_out);
+// The handle's observables reduction into acc[NACC] (synchronises).
+int reduce_handle(ltne_handle* h, double* acc);
+}  // namespace ltne

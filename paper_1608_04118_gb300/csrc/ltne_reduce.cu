@@ -48,15 +48,20 @@ __device__ void block_reduce(double (&acc)[NACC], double* sh /* [RB/32][NACC] */
 // each thread walks its column down the segment (coalesced rows across the
 // warp), accumulating in the fields' own precision C over at most SEG nodes,
 // then everything from the per-thread partials upward is combined in FP64.
+// Rows go in groups of RU (4 in FP32, 2 in FP64, which holds twice the
+// registers per value): all loads of a group are issued before any of its
+// snapshot stores, so a thread keeps RU rows of loads in flight.
 template <typename C>
 __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a) {
+  constexpr int RU = sizeof(C) == 4 ? 4 : 2;
   __shared__ double sh[(RB / 32) * NACC];
   C acc[NACC];
 #pragma unroll
   for (int k = 0; k < NACC; ++k) acc[k] = C(0);
-  const C* mac = static_cast<const C*>(a.mac);
-  const C* phi_f = static_cast<const C*>(a.phi);
-  C* prev = static_cast<C*>(a.prev);
+  const C* __restrict__ mac = static_cast<const C*>(a.mac);
+  const C* __restrict__ phi_f = static_cast<const C*>(a.phi);
+  C* __restrict__ prev = static_cast<C*>(a.prev);
+  const int64_t pl = a.plane;
   const int x = blockIdx.x * RB + threadIdx.x;
   const int y0 = blockIdx.y * SEG;
   const int y1 = min(y0 + SEG, a.ny);
@@ -66,43 +71,66 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a) {
   const C whot = (x == 1) ? C(-2) : (x == 2) ? C(0.5) : C(0);
   const C wcold = (x == a.nx - 2) ? C(2) : (x == a.nx - 3) ? C(-0.5) : C(0);
   if (x < a.nx) {
-    for (int y = y0; y < y1; ++y) {
-      const int64_t off = (int64_t)y * a.pitch + x;
-      // deviations: rho - 1, ux, uy, T_f - T0, T_s - T0
-      const C rho = mac[off], ux = mac[a.plane + off], uy = mac[2 * a.plane + off];
-      const C Tf = mac[3 * a.plane + off], Ts = mac[4 * a.plane + off];
-      const C phi = phi_f ? phi_f[off] : phi_u;
-      const C wy = (y == 0 || y == a.ny - 1) ? C(0.5) : C(1);
-      acc[A_NUF_H] += whot * wy * Tf;
-      acc[A_NUS_H] += whot * wy * Ts;
-      acc[A_NUF_C] += wcold * wy * Tf;
-      acc[A_NUS_C] += wcold * wy * Ts;
-      acc[A_MASS] += rho;
-      // deviation part of phi T_f + (1-phi) sigma T_s; the T0 and Q parts
-      // are restored from the porosity sum in FP64
-      acc[A_ENERGY] += phi * Tf + (C(1) - phi) * sigma * Ts;
-      acc[A_SUMPHI] += phi;
-      const C u2 = ux * ux + uy * uy;
-      acc[A_MAXU] = u2 > acc[A_MAXU] ? u2 : acc[A_MAXU];  // |u|^2, rooted in FP64
-      const C dT = Tf > Ts ? Tf - Ts : Ts - Tf;
-      acc[A_MAXDT] = dT > acc[A_MAXDT] ? dT : acc[A_MAXDT];
-      acc[A_SUMTF] += Tf;
-      acc[A_SUMTS] += Ts;
-      const C pux = prev[off], puy = prev[a.plane + off];
-      const C pTf = prev[2 * a.plane + off], pTs = prev[3 * a.plane + off];
-      acc[A_DU2] += (ux - pux) * (ux - pux) + (uy - puy) * (uy - puy);
-      acc[A_U2] += u2;
-      acc[A_DTF2] += (Tf - pTf) * (Tf - pTf);
-      acc[A_TF2] += Tf * Tf;
-      acc[A_DTS2] += (Ts - pTs) * (Ts - pTs);
-      acc[A_TS2] += Ts * Ts;
-      if (!(isfinite(rho) && isfinite(ux) && isfinite(uy) && isfinite(Tf) && isfinite(Ts)))
-        acc[A_BAD] += C(1);
+    for (int yg = y0; yg < y1; yg += RU) {
+      // deviations: rho - 1, ux, uy, T_f - T0, T_s - T0; the previous
+      // snapshot of ux, uy, T_f, T_s
+      C rho[RU], ux[RU], uy[RU], Tf[RU], Ts[RU], phi[RU], pux[RU], puy[RU], pTf[RU], pTs[RU];
+#pragma unroll
+      for (int r = 0; r < RU; ++r) {
+        const int y = min(yg + r, y1 - 1);  // a short last group re-reads its last row
+        const int64_t off = (int64_t)y * a.pitch + x;
+        rho[r] = mac[off];
+        ux[r] = mac[pl + off];
+        uy[r] = mac[2 * pl + off];
+        Tf[r] = mac[3 * pl + off];
+        Ts[r] = mac[4 * pl + off];
+        phi[r] = phi_f ? phi_f[off] : phi_u;
+        pux[r] = prev[off];
+        puy[r] = prev[pl + off];
+        pTf[r] = prev[2 * pl + off];
+        pTs[r] = prev[3 * pl + off];
+      }
+#pragma unroll
+      for (int r = 0; r < RU; ++r) {
+        const int y = yg + r;
+        if (y >= y1) break;
+        const C wy = (y == 0 || y == a.ny - 1) ? C(0.5) : C(1);
+        acc[A_NUF_H] += whot * wy * Tf[r];
+        acc[A_NUS_H] += whot * wy * Ts[r];
+        acc[A_NUF_C] += wcold * wy * Tf[r];
+        acc[A_NUS_C] += wcold * wy * Ts[r];
+        acc[A_MASS] += rho[r];
+        // deviation part of phi T_f + (1-phi) sigma T_s; the T0 and Q parts
+        // are restored from the porosity sum in FP64
+        acc[A_ENERGY] += phi[r] * Tf[r] + (C(1) - phi[r]) * sigma * Ts[r];
+        acc[A_SUMPHI] += phi[r];
+        const C u2 = ux[r] * ux[r] + uy[r] * uy[r];
+        acc[A_MAXU] = u2 > acc[A_MAXU] ? u2 : acc[A_MAXU];  // |u|^2, rooted in FP64
+        const C dT = Tf[r] > Ts[r] ? Tf[r] - Ts[r] : Ts[r] - Tf[r];
+        acc[A_MAXDT] = dT > acc[A_MAXDT] ? dT : acc[A_MAXDT];
+        acc[A_SUMTF] += Tf[r];
+        acc[A_SUMTS] += Ts[r];
+        acc[A_DU2] += (ux[r] - pux[r]) * (ux[r] - pux[r]) + (uy[r] - puy[r]) * (uy[r] - puy[r]);
+        acc[A_U2] += u2;
+        acc[A_DTF2] += (Tf[r] - pTf[r]) * (Tf[r] - pTf[r]);
+        acc[A_TF2] += Tf[r] * Tf[r];
+        acc[A_DTS2] += (Ts[r] - pTs[r]) * (Ts[r] - pTs[r]);
+        acc[A_TS2] += Ts[r] * Ts[r];
+        if (!(isfinite(rho[r]) && isfinite(ux[r]) && isfinite(uy[r]) && isfinite(Tf[r]) &&
+              isfinite(Ts[r])))
+          acc[A_BAD] += C(1);
+      }
       if (a.update_prev) {
-        prev[off] = ux;
-        prev[a.plane + off] = uy;
-        prev[2 * a.plane + off] = Tf;
-        prev[3 * a.plane + off] = Ts;
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const int y = yg + r;
+          if (y >= y1) break;
+          const int64_t off = (int64_t)y * a.pitch + x;
+          prev[off] = ux[r];
+          prev[pl + off] = uy[r];
+          prev[2 * pl + off] = Tf[r];
+          prev[3 * pl + off] = Ts[r];
+        }
       }
     }
   }

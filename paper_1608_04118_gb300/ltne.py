@@ -102,7 +102,7 @@ SIGNATURES = {
     "ltne_batch_workspace_bytes": (C.c_size_t, [_vp]),
     "ltne_batch_nodes": (C.c_int64, [_vp]),
     "ltne_batch_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
-    "ltne_batch_set_schedule": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+    "ltne_batch_set_schedule": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "ltne_batch_set_fields": (C.c_int, [_vp]),
     "ltne_batch_step": (C.c_int, [_vp, C.c_int64]),
     "ltne_batch_observables": (C.c_int, [_vp, C.POINTER(ltne_obs)]),
@@ -385,8 +385,9 @@ def ltne_batch_bind_workspace(b, device_ptr: int, nbytes: int):
            "ltne_batch_bind_workspace")
 
 
-def ltne_batch_set_schedule(b, tile_x, tile_y, blocks):
-    _check(_lib().ltne_batch_set_schedule(b, int(tile_x), int(tile_y), int(blocks)),
+def ltne_batch_set_schedule(b, tile_x, tile_y, blocks, nodes_per_thread=1):
+    _check(_lib().ltne_batch_set_schedule(b, int(tile_x), int(tile_y), int(blocks),
+                                          int(nodes_per_thread)),
            "ltne_batch_set_schedule")
 
 
@@ -446,7 +447,7 @@ class Batch:
         nbytes = ltne_batch_workspace_bytes(self.b)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         ltne_batch_bind_workspace(self.b, self.workspace.data_ptr(), nbytes)
-        self.schedule = (128, 2, 0)
+        self.schedule = (128, 2, 0, 1)
 
     @property
     def count(self):
@@ -456,9 +457,9 @@ class Batch:
     def nodes(self):
         return ltne_batch_nodes(self.b)
 
-    def set_schedule(self, tile_x, tile_y, blocks):
-        ltne_batch_set_schedule(self.b, tile_x, tile_y, blocks)
-        self.schedule = (tile_x, tile_y, blocks)
+    def set_schedule(self, tile_x, tile_y, blocks, nodes_per_thread=1):
+        ltne_batch_set_schedule(self.b, tile_x, tile_y, blocks, nodes_per_thread)
+        self.schedule = (tile_x, tile_y, blocks, nodes_per_thread)
         return self
 
     def set_fields(self):

@@ -149,7 +149,7 @@ def test_option_validation_without_gpu(lt):
     assert lt.ltne_batch_nodes(b) == 32 * 32 + 64 * 32
     assert lt.ltne_batch_workspace_bytes(b) > 2 * 19 * 4 * (32 * 32 + 64 * 32)
     # a schedule needs a bound workspace
-    assert lib.ltne_batch_set_schedule(b, 64, 2, 0) == lt.LTNE_ERR_STATE
+    assert lib.ltne_batch_set_schedule(b, 64, 2, 0, 1) == lt.LTNE_ERR_STATE
     lt.ltne_batch_destroy(b)
     # the adjoint needs a bound workspace and rejects the local h_v model
     p = lt.ltne_default_params(32, 32, porosity_field=1, hv_local=1)
@@ -165,8 +165,14 @@ def test_option_validation_without_gpu(lt):
     # float arithmetic and at most 128 threads per block
     for storage, default in ((lt.LTNE_F32, (128, 1, 2)), (lt.LTNE_F16DEV, (32, 4, 2)),
                              (lt.LTNE_BF16DEV, (32, 4, 2)), (lt.LTNE_F64, (128, 2, 1))):
+        h = lt.ltne_create(lt.ltne_default_params(1024, 1024, storage=storage))
+        assert lt.ltne_get_schedule(h) == default  # 2^20 nodes: the large-lattice default
+        lt.ltne_destroy(h)
+        h = lt.ltne_create(lt.ltne_default_params(1024, 1023, storage=storage))
+        assert lt.ltne_get_schedule(h) == (128, 2, 1)
+        lt.ltne_destroy(h)
         h = lt.ltne_create(lt.ltne_default_params(32, 32, storage=storage))
-        assert lt.ltne_get_schedule(h) == default
+        assert lt.ltne_get_schedule(h) == (128, 2, 1)
         for bad in ((48, 2, 1), (16, 1, 1), (512, 1, 1), (128, 4, 1), (128, 2, 3), (128, 0, 1),
                     (64, 4, 2), (256, 1, 2)):
             assert lib.ltne_set_schedule(h, *bad) == lt.LTNE_ERR_INVALID_ARG, bad

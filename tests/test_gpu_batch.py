@@ -46,10 +46,15 @@ def test_small_batch_matches_oracle_per_cavity():
             assert err[k] <= 1e-5, (i, c["nx"], c["ny"], k, err)
 
 
-def test_schedule_does_not_change_results():
+@pytest.mark.parametrize("schedules", [
+    ((128, 2, 0, 1), (32, 4, 3, 1), (64, 2, 152, 1), (256, 1, 1, 1)),
+    ((64, 2, 0, 2), (128, 1, 5, 2), (256, 1, 152, 2), (64, 4, 1, 2))])
+def test_schedule_does_not_change_results(schedules):
+    """Tile shape and grid size change no bit for a fixed number of nodes per
+    thread (one, or two in paired FP32 arithmetic)."""
     cavs = small_batch(8, seed=71)
     runs = []
-    for sch in ((128, 2, 0), (32, 4, 3), (64, 2, 152), (256, 1, 1)):
+    for sch in schedules:
         b = _batch(cavs).set_schedule(*sch).set_fields().step(77)
         runs.append([b.fields(i) for i in range(len(cavs))])
     for r in runs[1:]:
@@ -58,12 +63,14 @@ def test_schedule_does_not_change_results():
                 assert np.array_equal(a[k], c[k]), k
 
 
-def test_batch_equals_single_lattice_path():
+@pytest.mark.parametrize("npt", [1, 2])
+def test_batch_equals_single_lattice_path(npt):
     cavs = small_batch(6, seed=72)
-    b = _batch(cavs).set_fields().step(120)
+    b = _batch(cavs).set_schedule(128 if npt == 1 else 64, 2, 0, npt).set_fields().step(120)
     obs = b.observables()
     for i, c in enumerate(cavs):
-        s = cavity_for(c, storage="f32").set_fields().step(120)
+        s = cavity_for(c, storage="f32").set_schedule(128 if npt == 1 else 64, 2, npt)
+        s = s.set_fields().step(120)
         fs, fb = s.fields(), b.fields(i)
         for k in fs:
             assert np.allclose(fb[k], fs[k], rtol=0, atol=1e-6 * max(1.0, np.abs(fs[k]).max())), k

@@ -181,16 +181,17 @@ def test_reduced_storage_64_cavity_10k_steps(storage, tol):
         assert err[k] <= tol, (storage, k, err)
 
 
+@pytest.mark.parametrize("schedule", [(128, 2, 1), (32, 4, 2)])
 @pytest.mark.parametrize("storage,tol_u,tol_T,tol_nu", [("f32", 1e-5, 1e-5, 1e-4),
                                                         ("f16", 1e-3, 1e-3, 2e-3),
                                                         ("bf16", 6e-3, 2e-3, 2e-2)])
-def test_reduced_storage_512_parity_run(storage, tol_u, tol_T, tol_nu):
+def test_reduced_storage_512_parity_run(storage, tol_u, tol_T, tol_nu, schedule):
     """Physics of the reduced-storage configuration (Ra 1e6, H 1000, phi 0.6,
     Da 1e-2) on the down-sized 512 x 512 cavity for 2000 steps: per-field
     relative L2 errors against the FP64 oracle."""
     cfg = dict(W.C5_REDUCED, nx=W.C5_REDUCED["parity_n"], ny=W.C5_REDUCED["parity_n"])
     ref = _c5_oracle(cfg)
-    c = cavity_for(cfg, storage=storage).set_fields().step(cfg["steps"])
+    c = cavity_for(cfg, storage=storage).set_schedule(*schedule).set_fields().step(cfg["steps"])
     err = field_errors(c.fields(), ref["fields"])
     assert err["u"] <= tol_u, err
     assert err["Tf"] <= tol_T and err["Ts"] <= tol_T, err

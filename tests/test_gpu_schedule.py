@@ -95,13 +95,14 @@ def test_block_shape_changes_no_bit(storage, npt):
             assert np.array_equal(f[k], ref[k]), (shape, k)
 
 
+@pytest.mark.parametrize("schedule", [(128, 2, 1), (32, 4, 2)])
 @pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", 1e-2)])
-def test_reduced_storage_one_node_form_64_cavity(storage, tol):
-    """The one-node form of the 16-bit kernels on the 64 x 64 cavity after
-    10^4 steps (the default two-node form is covered by the parity suite)."""
+def test_reduced_storage_both_forms_64_cavity(storage, tol, schedule):
+    """Both forms of the 16-bit kernels on the 64 x 64 cavity after 10^4
+    steps against the oracle."""
     cfg = W.C1_PLAIN_64
     o = oracle_for(cfg).init().step(cfg["steps"])
-    c = cavity_for(cfg, storage=storage).set_schedule(128, 2, 1).set_fields().step(cfg["steps"])
+    c = cavity_for(cfg, storage=storage).set_schedule(*schedule).set_fields().step(cfg["steps"])
     err = field_errors(c.fields(), o.macros())
     for k in ("u", "Tf", "Ts"):
         assert err[k] <= tol, (storage, k, err)
