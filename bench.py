@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--batch-schedule", default="",
                     help="c3: tile_x,tile_y,blocks,nodes_per_thread instead of the autotuned "
                          "schedule")
+    ap.add_argument("--no-context", action="store_true",
+                    help="c4: skip the 1024^2 context run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -423,7 +425,7 @@ def run_adjoint(args):
     from paper_1608_04118_gb300.ltne import Cavity, LTNE_K_ERGUN
 
     c = W.C4_ADJOINT
-    nx, ny = c["nx"], c["ny"]
+    nx, ny = (c["nx"], c["ny"]) if args.n == 4096 else (args.n, args.n)
     steps = args.steps if args.steps != 2000 else c["steps"]
     seg = int(math.ceil(math.sqrt(steps)))
     phi = W.porosity_field(nx, ny, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
@@ -476,13 +478,14 @@ def run_adjoint(args):
         return {"n": n, "steps": k, "segment": sg, "mlups": n * n * k / ta / 1e6,
                 "plain_forward_mlups": n * n * k / tf / 1e6, "ratio_to_plain_forward": tf / ta}
 
-    big = at_size(1024, 1000)
-    line = {"metric": "MLUPS (forward + adjoint, 256x256)", "value": nodes * steps / t_adj / 1e6,
+    big = None if args.no_context else at_size(1024, 1000)
+    line = {"metric": "MLUPS (forward + adjoint, %dx%d)" % (nx, ny),
+            "value": nodes * steps / t_adj / 1e6,
             "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "porous LTNE cavity 256x256, porosity U[0.4,0.8] seed 4, "
-                                   "Ergun mean Da 1e-3, Ra 1e5, H 50", "segment": seg,
+            "config": {"workload": "porous LTNE cavity %dx%d, porosity U[0.4,0.8] seed 4, "
+                                   "Ergun mean Da 1e-3, Ra 1e5, H 50" % (nx, ny), "segment": seg,
                        "objective": "(Nu_f,hot + Nu_s,hot)/2 at the last step"},
             "seconds": t_adj, "plain_forward_mlups": nodes * steps / t_fwd / 1e6,
             "ratio_to_plain_forward": (nodes * steps / t_adj) / (nodes * steps / t_fwd),

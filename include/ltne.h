@@ -213,6 +213,43 @@ int64_t ltne_launch_count(const ltne_handle* h);
    LTNE_ERR_INVALID_ARG for other schedules. */
 int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
                       int32_t nodes_per_thread);
+
+/* Staged tiles (no counterpart in the paper): staged = 1 runs the step as
+   the two-node kernel whose persistent blocks stream tiles of
+   (2 block_x) x block_y nodes, with a halo of one row and 16 bytes of
+   columns, from HBM into shared memory by the tensor memory accelerator,
+   several tiles ahead, instead of loading each node's values directly
+   (FP32, FP16, BF16 storage with cavity walls only; block shapes 32 x 4,
+   64 x 2 or 32 x 2 threads, any other shape runs as 32 x 4).  Results are
+   the same bits as the direct two-node schedule.  A staged step whose tile never
+   arrives gives up after about a second and makes the next
+   ltne_observables return LTNE_ERR_TIMEOUT.  staged = 0 (default) returns
+   to the schedule.  LTNE_ERR_INVALID_ARG for other storage or walls. */
+int ltne_set_staging(ltne_handle* h, int32_t staged);
+int ltne_get_staging(const ltne_handle* h, int32_t* staged);
+
+/* Row-slab decomposition on one device (no counterpart in the paper; the
+   decomposition a multi-GPU run would use, checked here without a second
+   GPU).  ltne_step_slabs advances the lattice n steps as nslabs slabs of
+   consecutive rows, each with its own population buffers in `scratch`
+   (caller-owned device memory of ltne_slab_scratch_bytes bytes, 256-byte
+   aligned) and one halo row towards each neighbouring slab: after every
+   step the slabs' boundary rows (all 19 planes) are copied into the
+   neighbours' halo rows by device-to-device copies, then the computed rows
+   and the macroscopic fields are gathered back into the handle.  The
+   result is the same bits as ltne_step(h, n).  Cavity walls, FP32 or FP64
+   storage, no local h_v, at least 2 rows per slab; otherwise
+   ltne_slab_scratch_bytes returns 0 and ltne_step_slabs
+   LTNE_ERR_INVALID_ARG.  Asynchronous on the handle's stream. */
+size_t ltne_slab_scratch_bytes(const ltne_handle* h, int32_t nslabs);
+int ltne_step_slabs(ltne_handle* h, int32_t nslabs, int64_t n, void* scratch, size_t bytes);
+
+/* Self-check of the bounded wait of the staged step (no counterpart in the
+   paper): one GPU thread waits, with at most `spins` polls, on an mbarrier
+   phase that can never complete; *gave_up = 1 when the wait returned
+   without it, as it must.  Allocates 4 bytes of device memory on the
+   stream; synchronises it. */
+int ltne_check_bounded_wait(void* cuda_stream, int32_t spins, int32_t* gave_up);
 int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
                       int32_t* nodes_per_thread);
 

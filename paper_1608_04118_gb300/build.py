@@ -10,6 +10,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import hashlib
+import re
 import os
 import shutil
 import subprocess
@@ -49,16 +50,25 @@ def _fingerprint(extra_flags=()) -> str:
     return h.hexdigest()
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed, so
+    that editing a comment does not count as changing the code."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the sources that define the step kernel (used to tell whether
-    stored profiler counters still describe the current kernel)."""
+    """Hash of the code (comments excluded) of the sources that define the
+    step kernel (used to tell whether stored profiler counters still
+    describe the current kernel)."""
     h = hashlib.sha256()
     names = ["ltne_node.cuh", "ltne_step_impl.cuh", "ltne_pair.cuh", "ltne_internal.h"] + sorted(
         os.path.basename(f) for f in glob.glob(os.path.join(CSRC, "step_*.cu")))
     for n in names:
-        with open(os.path.join(CSRC, n), "rb") as fh:
+        with open(os.path.join(CSRC, n)) as fh:
             h.update(n.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

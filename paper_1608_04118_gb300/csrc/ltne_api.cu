@@ -385,8 +385,8 @@ void layout(ltne_handle* h) {
   off = align_up(off + (size_t)h->red_blocks * NACC * sizeof(double), A);
   h->off_out = off;
   off = align_up(off + NACC * sizeof(double), A);
-  h->off_tick = off;  // two uint32 step counters for the stochastic rounding
-  off = align_up(off + 2 * sizeof(uint32_t), A);
+  h->off_tick = off;  // two uint32 step counters for the stochastic rounding, then
+  off = align_up(off + 3 * sizeof(uint32_t), A);  // the device error word
   for (int b = 0; b < 2; ++b) {  // |u| of the previous state per buffer (Eq. 52)
     h->off_um[b] = off;
     if (p.hv_local) off = align_up(off + (size_t)h->plane * h->ec, A);
@@ -411,6 +411,7 @@ LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
   uint32_t* tick = reinterpret_cast<uint32_t*>(h->ws + h->off_tick);
   a.tick_in = tick + src_buf;
   a.tick_out = tick + (src_buf ^ 1);
+  a.err = reinterpret_cast<int*>(tick + 2);
   if (h->p.hv_local) {
     a.um_in = h->ws + h->off_um[src_buf];
     a.um_out = h->ws + h->off_um[src_buf ^ 1];
@@ -443,7 +444,9 @@ cudaError_t build_graph(ltne_handle* h, int parity) {
     e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
   }
-  e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  // relaxed: a launcher may query the occupancy or set a kernel attribute
+  // the first time it runs, which can happen inside this capture
+  e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return e;
   int b = parity;
   cudaError_t le = cudaSuccess;
@@ -490,6 +493,15 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   if (rc != LTNE_OK) return rc;
   drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
 
+  // Zero the whole workspace first -- population buffers, porosity,
+  // macroscopic fields, residual snapshot, |u| planes, counters -- so that
+  // row and plane padding, which no kernel writes, is zero and state blobs
+  // are deterministic.
+  {
+    const cudaError_t ez = cudaMemsetAsync(h->ws, 0, h->ws_bytes, h->stream);
+    if (ez != cudaSuccess) return fail_cuda(ez);
+  }
+
   // Stage the fields as deviations (rho - 1, ux, uy, T - T_ref; compute
   // type) into the macro planes, then k_init.
   const double defaults[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
@@ -524,12 +536,8 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
     rc = stage(porosity, 0.0, 0.0, h->ws + h->off_phi);
     if (rc != LTNE_OK) return rc;
   }
-  // Zero both population buffers (row padding included, so that state
-  // blobs are deterministic) and the residual snapshot.
-  cudaError_t e = cudaMemsetAsync(h->ws + h->off_pop[0], 0, h->off_phi - h->off_pop[0], h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(h->ws + h->off_prev, 0, 4 * (size_t)h->plane * h->ec, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->off_tick, 0, 2 * sizeof(uint32_t), h->stream);
+  // the step counters and the device error word start cleared
+  cudaError_t e = cudaMemsetAsync(h->ws + h->off_tick, 0, 3 * sizeof(uint32_t), h->stream);
   if (e != cudaSuccess) return fail_cuda(e);
   LatticeArgs a = lattice_args(h, 1, 1);  // dst = buffer 0
   a.pre_out = pre_out;
@@ -575,6 +583,66 @@ int reduce_handle(ltne_handle* h, double* acc) {
 }
 
 }  // namespace ltne
+
+// ---- row-slab decomposition on one device ---------------------------------
+//
+// Slab p holds rows [g0, g0 + rows) of the cavity, plus one halo row below
+// (p > 0) and one above (p < nslabs - 1) with the neighbouring slabs' values;
+// its first / last row is otherwise the cavity's bottom / top wall row.
+namespace {
+
+struct SlabGeom {
+  int g0, rows, lo, hi;  // first global row, computed rows, halo rows below / above
+  int ny;                // local rows: rows + lo + hi
+  int64_t plane;         // local plane (elements)
+  size_t off_pop[2], off_phi, off_mac, end;  // byte offsets in the scratch
+};
+
+std::vector<SlabGeom> slab_layout(const ltne_handle* h, int nslabs) {
+  std::vector<SlabGeom> g((size_t)nslabs);
+  const int ny = h->p.ny, base = ny / nslabs, extra = ny % nslabs;
+  size_t off = 0;
+  int y = 0;
+  for (int p = 0; p < nslabs; ++p) {
+    SlabGeom& s = g[(size_t)p];
+    s.g0 = y;
+    s.rows = base + (p < extra ? 1 : 0);
+    y += s.rows;
+    s.lo = p > 0;
+    s.hi = p < nslabs - 1;
+    s.ny = s.rows + s.lo + s.hi;
+    s.plane = (int64_t)align_up((size_t)(h->pitch * s.ny), 128);
+    for (int b = 0; b < 2; ++b) {
+      s.off_pop[b] = off;
+      off = align_up(off + 19 * (size_t)s.plane * h->es, 256);
+    }
+    s.off_phi = off;
+    if (h->p.porosity_field) off = align_up(off + (size_t)s.plane * h->ec, 256);
+    s.off_mac = off;
+    off = align_up(off + 5 * (size_t)s.plane * h->ec, 256);
+    s.end = off;
+  }
+  return g;
+}
+
+bool slabs_supported(const ltne_handle* h, int nslabs) {
+  return h && nslabs >= 1 && h->p.bc == LTNE_BC_CAVITY && !h->p.hv_local &&
+         (h->p.storage == LTNE_F32 || h->p.storage == LTNE_F64) && h->p.ny / nslabs >= 2;
+}
+
+// Copies `nrows` rows starting at src_row of `planes` planes (plane strides
+// in elements, row pitch shared) between two plane sets: one 2-D copy whose
+// rows are the planes' row blocks.
+cudaError_t copy_rows(char* dst, int64_t dplane, int dst_row, const char* src, int64_t splane,
+                      int src_row, int nrows, int planes, int64_t pitch, size_t esz,
+                      cudaStream_t st) {
+  const size_t w = (size_t)nrows * pitch * esz;
+  return cudaMemcpy2DAsync(dst + (size_t)dst_row * pitch * esz, (size_t)dplane * esz,
+                           src + (size_t)src_row * pitch * esz, (size_t)splane * esz, w,
+                           (size_t)planes, cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -706,6 +774,17 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   double acc[NACC];
   const int rr = reduce_handle(h, acc);
   if (rr != LTNE_OK) return rr;
+  // a staged step that gave up waiting for its tile reports here (the
+  // fields are then not trustworthy); the word is cleared
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, h->ws + h->off_tick + 2 * sizeof(uint32_t), sizeof(err),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  if (err) {
+    e = cudaMemsetAsync(h->ws + h->off_tick + 2 * sizeof(uint32_t), 0, sizeof(err), h->stream);
+    return e == cudaSuccess ? LTNE_ERR_TIMEOUT : fail_cuda(e);
+  }
   DerivedInfo info;
   info.L = h->L;
   info.nu_f = h->nu_f;
@@ -813,9 +892,12 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
       drop_graphs(h);
     }
   }
-  const uint32_t tick = (uint32_t)hdr[4];  // the rounding stream is keyed by the step
+  // the rounding stream is keyed by the step; the other counter slot and
+  // the device error word start cleared
+  const uint32_t words[3] = {(uint32_t)hdr[4], 0u, 0u};
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->ws + h->off_tick, &tick, sizeof(tick), cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(h->ws + h->off_tick, words, sizeof(words), cudaMemcpyHostToDevice,
+                        h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail_cuda(e);
   h->cur = 0;
@@ -840,6 +922,97 @@ int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
   h->shape.by = block_y;
   h->shape.pair = nodes_per_thread == 2 ? 1 : 0;
   drop_graphs(h);  // the captured launches carry the old configuration
+  return LTNE_OK;
+}
+
+size_t ltne_slab_scratch_bytes(const ltne_handle* h, int32_t nslabs) {
+  if (!slabs_supported(h, nslabs)) return 0;
+  return slab_layout(h, nslabs).back().end;
+}
+
+int ltne_step_slabs(ltne_handle* h, int32_t nslabs, int64_t n, void* scratch, size_t bytes) {
+  if (!slabs_supported(h, nslabs) || n < 0) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  const std::vector<SlabGeom> g = slab_layout(h, nslabs);
+  char* ws = static_cast<char*>(scratch);
+  if (!ws || bytes < g.back().end || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+    return LTNE_ERR_WORKSPACE;
+  if (n == 0) return LTNE_OK;
+  const int64_t pitch = h->pitch;
+  const size_t es = h->es, ec = h->ec;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  // zeroed slab buffers keep the row padding of the gathered planes zero (as
+  // in the handle), then scatter the current populations (halo rows
+  // included) and the porosity
+  e = cudaMemsetAsync(ws, 0, g.back().end, st);
+  if (e != cudaSuccess) return fail_cuda(e);
+  for (const SlabGeom& s : g) {
+    e = copy_rows(ws + s.off_pop[0], s.plane, 0, h->ws + h->off_pop[h->cur], h->plane,
+                  s.g0 - s.lo, s.ny, 19, pitch, es, st);
+    if (e == cudaSuccess && h->p.porosity_field)
+      e = copy_rows(ws + s.off_phi, s.plane, 0, h->ws + h->off_phi, h->plane, s.g0 - s.lo, s.ny,
+                    1, pitch, ec, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  StepShape one;  // one node per thread, 128 x 2
+  int b = 0;
+  for (int64_t k = 0; k < n && e == cudaSuccess; ++k) {
+    for (const SlabGeom& s : g) {
+      LatticeArgs a = lattice_args(h, h->cur, k == n - 1 ? 1 : 0);
+      a.src = ws + s.off_pop[b];
+      a.dst = ws + s.off_pop[b ^ 1];
+      a.phi = h->p.porosity_field ? ws + s.off_phi : nullptr;
+      a.mac = ws + s.off_mac;
+      a.ny = s.ny;
+      a.plane = s.plane;
+      a.bc = BC_SLAB;
+      a.slab_walls = (s.lo ? 0 : SLAB_LO_WALL) | (s.hi ? 0 : SLAB_HI_WALL);
+      e = h->p.storage == LTNE_F64 ? launch_step_f64(a, h->P, one, st)
+                                   : launch_step_f32(a, h->P, one, st);
+      if (e != cudaSuccess) break;
+    }
+    // halo exchange across every cut: the lower slab's last computed row to
+    // the upper slab's halo below, the upper slab's first to the lower's halo above
+    for (int p = 0; p + 1 < nslabs && e == cudaSuccess; ++p) {
+      const SlabGeom &lo = g[(size_t)p], &up = g[(size_t)p + 1];
+      e = copy_rows(ws + up.off_pop[b ^ 1], up.plane, 0, ws + lo.off_pop[b ^ 1], lo.plane,
+                    lo.lo + lo.rows - 1, 1, 19, pitch, es, st);
+      if (e == cudaSuccess)
+        e = copy_rows(ws + lo.off_pop[b ^ 1], lo.plane, lo.ny - 1, ws + up.off_pop[b ^ 1],
+                      up.plane, up.lo, 1, 19, pitch, es, st);
+    }
+    b ^= 1;
+  }
+  if (e != cudaSuccess) return fail_cuda(e);
+  // gather the computed rows and the macroscopic fields of the last step
+  const int out = h->cur ^ (int)(n & 1);
+  for (const SlabGeom& s : g) {
+    e = copy_rows(h->ws + h->off_pop[out], h->plane, s.g0, ws + s.off_pop[b], s.plane, s.lo,
+                  s.rows, 19, pitch, es, st);
+    if (e == cudaSuccess)
+      e = copy_rows(h->ws + h->off_mac, h->plane, s.g0, ws + s.off_mac, s.plane, s.lo, s.rows, 5,
+                    pitch, ec, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+  }
+  h->cur = out;
+  h->step += n;
+  h->launches += n * nslabs;
+  return LTNE_OK;
+}
+
+int ltne_set_staging(ltne_handle* h, int32_t staged) {
+  if (!h || (staged != 0 && staged != 1)) return LTNE_ERR_INVALID_ARG;
+  if (staged && (h->p.storage == LTNE_F64 || h->p.bc != LTNE_BC_CAVITY))
+    return LTNE_ERR_INVALID_ARG;
+  h->shape.tma = staged;
+  drop_graphs(h);
+  return LTNE_OK;
+}
+
+int ltne_get_staging(const ltne_handle* h, int32_t* staged) {
+  if (!h || !staged) return LTNE_ERR_INVALID_ARG;
+  *staged = h->shape.tma;
   return LTNE_OK;
 }
 

@@ -10,6 +10,13 @@
 
 namespace ltne {
 
+// Boundary modes (values of LTNE_BC_*), and BC_SLAB: a row slab of a cavity
+// (left/right walls; its first and last rows are either the cavity's
+// bottom/top wall rows or halo rows holding the neighbouring slabs' values,
+// which are read but not updated).
+constexpr int BC_CAVITY = 0, BC_PERIODIC = 1, BC_CHANNEL = 2, BC_SLAB = 3;
+constexpr int SLAB_LO_WALL = 1, SLAB_HI_WALL = 2;  // bits of slab_walls
+
 // Geometry and buffers of one lattice as the kernels see it.  Populations
 // are structure-of-arrays planes, index q*plane + y*pitch + x, in the order
 // f_0..f_8, g_f0..g_f4, g_s0..g_s4.  Rows are padded to a multiple of 64
@@ -30,6 +37,8 @@ struct LatticeArgs {
   void* pre_out;            // k_init: also record S_0 here (compute type), or nullptr
   const void* um_in;        // |u| plane of the previous state (local h_v), or nullptr
   void* um_out;             // |u| plane written for the next state
+  int* err;                 // device error word: set by a bounded wait that gave up
+  int slab_walls;           // BC_SLAB: which of the first / last rows are walls
 };
 
 // Launch configuration of the step kernel: a block of bx x by threads,
@@ -40,6 +49,7 @@ struct StepShape {
   int bx = 128;
   int by = 2;
   int pair = 0;
+  int tma = 0;  // two nodes per thread from TMA-staged tiles (cavity walls only)
 };
 
 // Per-storage-type launchers (one translation unit each).

@@ -471,20 +471,14 @@ template <> struct Codec<__half, float> {
   static __device__ __forceinline__ float dec(__half v, float inv_scale) {
     return __half2float(v) * inv_scale;
   }
-  // The deviation is scaled by 2^10 (exact) so that values down to ~6e-8
-  // stay in the normal FP16 range.  FP32 keeps 23 fraction bits and FP16 10:
-  // add 13 random bits below the kept ones and truncate, then convert (exact
-  // for normal FP16 values).  Fewer random bits would quantise the round-up
-  // probability, itself a bias for increments far below an ulp.
-  static __device__ __forceinline__ __half enc(float v, float scale, uint32_t r) {
-    uint32_t b = __float_as_uint(v * scale);
-    b = (b + (r & 0x1fffu)) & ~0x1fffu;
-    return __float2half_rn(__uint_as_float(b));
-  }
-  // Two values at once by the paired conversion with random bits (cvt.rs):
-  // lo takes bits 0-12 of r and goes to the low half, hi bits 16-28 and the
-  // high half -- the rounding of enc() above, value by value, in the normal
-  // FP16 range (below it the random bits sit under the subnormal ulp).
+  // Two values at once by the paired conversion with random bits
+  // (cvt.rs.f16x2.f32).  The deviations are scaled by 2^10 (exact) so that
+  // values down to ~6e-8 stay in the normal FP16 range.  Each value gets 13
+  // random bits added below its 10 kept fraction bits before truncation
+  // (FP32 keeps 23): lo takes bits 0-12 of r and goes to the low half, hi
+  // bits 16-28 and the high half; below the normal range the random bits
+  // sit under the subnormal ulp.  Fewer random bits would quantise the
+  // round-up probability, itself a bias for increments far below an ulp.
   static __device__ __forceinline__ uint32_t enc2(float lo, float hi, float scale, uint32_t r) {
     uint32_t d;
     asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi * scale), "f"(lo * scale), "r"(r));
@@ -496,12 +490,9 @@ template <> struct Codec<__nv_bfloat16, float> {
   static __device__ __forceinline__ float dec(__nv_bfloat16 v, float) {
     return __bfloat162float(v);
   }
-  // BF16 is the top half of FP32: add 16 random bits and truncate.
-  static __device__ __forceinline__ __nv_bfloat16 enc(float v, float, uint32_t r) {
-    const uint32_t b = __float_as_uint(v) + (r & 0xffffu);
-    return __ushort_as_bfloat16((unsigned short)(b >> 16));
-  }
-  // Two values at once (cvt.rs): lo with bits 0-15 of r, hi with bits 16-31.
+  // Two values at once (cvt.rs.bf16x2.f32): BF16 is the top half of FP32;
+  // 16 random bits are added below the kept ones and the result truncated,
+  // lo with bits 0-15 of r (low half), hi with bits 16-31 (high half).
   static __device__ __forceinline__ uint32_t enc2(float lo, float hi, float, uint32_t r) {
     uint32_t d;
     asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));

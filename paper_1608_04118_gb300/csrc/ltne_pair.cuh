@@ -118,12 +118,8 @@ template <> struct PairIO<__half> {
     return F2(mul2_(make_float2(__half2float(*a), __half2float(*b)),
                     make_float2(inv_scale, inv_scale)));
   }
-  // Stochastic rounding of both lanes by the paired conversion with
-  // random bits (cvt.rs): the first source goes to the upper half and takes
-  // the random bits 16-28, the second to the lower half with bits 0-12,
-  // each added below the kept fraction bits before truncation.  In the
-  // normal FP16 range this is the rounding of Codec<__half, float> bit for
-  // bit; below it the random bits are placed below the subnormal ulp.
+  // Both lanes in one paired conversion with random bits: the rounding of
+  // Codec<__half, float>::enc2 with the even node in the low half.
   static __device__ __forceinline__ void st2(__half* p, F2 v, float scale, uint32_t r) {
     const float2 w = mul2_(v.v, make_float2(scale, scale));
     uint32_t h;
@@ -141,9 +137,8 @@ template <> struct PairIO<__nv_bfloat16> {
                                             float) {
     return F2(__bfloat162float(*a), __bfloat162float(*b));
   }
-  // The paired conversion with random bits: 16 random bits added below
-  // the kept ones of each lane (upper half: bits 16-31 of r, lower half:
-  // bits 0-15), then truncation -- the rounding of Codec<__nv_bfloat16, float>.
+  // Both lanes in one paired conversion with random bits: the rounding of
+  // Codec<__nv_bfloat16, float>::enc2 with the even node in the low half.
   static __device__ __forceinline__ void st2(__nv_bfloat16* p, F2 v, float, uint32_t r) {
     uint32_t h;
     asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(h) : "f"(v.v.y), "f"(v.v.x), "r"(r));
@@ -225,6 +220,34 @@ __device__ __forceinline__ void st_f2(float* __restrict__ p, F2 v) {
   *reinterpret_cast<float2*>(p) = v.v;
 }
 
+// Everything after the pull for a pair at element offset off whose
+// pre-collision values are in f, gf, gs: macroscopic values, collision,
+// stores.  Shared by the pull from HBM and the pull from a staged tile.
+template <typename S>
+__device__ __forceinline__ void finish_pair(S* __restrict__ dst,
+                                            const float* __restrict__ phi_field,
+                                            float* __restrict__ mac, const NodeParams<F2>& P,
+                                            const uint32_t off, const uint32_t pl,
+                                            const float scale, const int write_macros,
+                                            const uint32_t tick, const float* __restrict__ um_in,
+                                            float* __restrict__ um_out, F2 (&f)[9], F2 (&gf)[5],
+                                            F2 (&gs)[5]) {
+  Medium<F2> md = phi_field ? medium_at<F2>(P, ld_f2(phi_field + off)) : P.um;
+  if (P.hv_local) set_exchange<F2>(md, hv_local_at<F2>(P, ld_f2(um_in + off)));
+  Macro<F2> m;
+  macros<F2>(P, md, f, gf, gs, m);
+  if (P.hv_local) st_f2(um_out + off, m.umag);
+  if (write_macros) {
+    st_f2(mac + off, m.drho);
+    st_f2(mac + pl + off, m.ux);
+    st_f2(mac + 2u * pl + off, m.uy);
+    st_f2(mac + 3u * pl + off, m.dTf);
+    st_f2(mac + 4u * pl + off, m.dTs);
+  }
+  collide<F2>(P, m, f, gf, gs);
+  PairPops<S>::store(dst, pl, off, scale, f, gf, gs, off, tick);
+}
+
 // The pair (x0, y), (x0 + 1, y) when both nodes exist and neither is a
 // left/right wall node: interior nodes, or both on a no-slip adiabatic row
 // (same rebuild, from the row above or below).
@@ -266,20 +289,8 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
     macros<F2>(P, mdn, f, gf, gs, mn);
     nee<F2>(P, mn, mn.dTf, mn.dTs, f, gf, gs);  // adiabatic: the neighbour's temperatures
   }
-  Medium<F2> md = phi_field ? medium_at<F2>(P, ld_f2(phi_field + off)) : P.um;
-  if (P.hv_local) set_exchange<F2>(md, hv_local_at<F2>(P, ld_f2(um_in + off)));
-  Macro<F2> m;
-  macros<F2>(P, md, f, gf, gs, m);
-  if (P.hv_local) st_f2(um_out + off, m.umag);
-  if (write_macros) {
-    st_f2(mac + off, m.drho);
-    st_f2(mac + pl + off, m.ux);
-    st_f2(mac + 2u * pl + off, m.uy);
-    st_f2(mac + 3u * pl + off, m.dTf);
-    st_f2(mac + 4u * pl + off, m.dTs);
-  }
-  collide<F2>(P, m, f, gf, gs);
-  PairPops<S>::store(dst, pl, off, scale, f, gf, gs, off, tick);
+  finish_pair<S>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out, f, gf,
+                 gs);
 }
 
 // Register budget of the pair kernel: blocks of at most 128 threads and at
@@ -347,17 +358,3 @@ cudaError_t launch_step_pair_t(const LatticeArgs& a, const NodeParams<double>& P
 }
 
 }  // namespace ltne
-
-// Launchers of a storage type with FP32 arithmetic: the schedule picks one
-// or two nodes per thread.
-#define LTNE_DEFINE_FLOAT_LAUNCHERS(tag, S)                                                     \
-  namespace ltne {                                                                             \
-  cudaError_t launch_step_##tag(const LatticeArgs& a, const NodeParams<double>& P,             \
-                                StepShape s, cudaStream_t st) {                                \
-    return s.pair ? launch_step_pair_t<S>(a, P, s, st) : launch_step_t<S, float>(a, P, s, st); \
-  }                                                                                            \
-  cudaError_t launch_init_##tag(const LatticeArgs& a, const NodeParams<double>& P,             \
-                                cudaStream_t st) {                                             \
-    return launch_init_t<S, float>(a, P, st);                                                  \
-  }                                                                                            \
-  }

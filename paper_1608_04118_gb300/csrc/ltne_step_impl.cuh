@@ -43,8 +43,6 @@ __host__ NodeParams<C> cast_params(const NodeParams<double>& d) {
   return p;
 }
 
-// Boundary modes (values of LTNE_BC_*).
-constexpr int BC_CAVITY = 0, BC_PERIODIC = 1, BC_CHANNEL = 2;
 
 template <typename S> __device__ __forceinline__ S bits_to(unsigned short b);
 template <> __device__ __forceinline__ __half bits_to<__half>(unsigned short b) {
@@ -139,19 +137,22 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
                                           const int write_macros, const uint32_t tick,
                                           C* __restrict__ pre_out = nullptr,
                                           const C* __restrict__ um_in = nullptr,
-                                          C* __restrict__ um_out = nullptr) {
+                                          C* __restrict__ um_out = nullptr,
+                                          const int slab_walls = 0) {
   // Wall classification and the node whose neighbourhood is pulled.
   int cx = x, cy = y;
   int kind = -1;  // -1 interior, 0 hot wall, 1 cold wall, 2 adiabatic / no-slip row
-  if (BC == BC_CAVITY) {
+  if (BC == BC_CAVITY || BC == BC_SLAB) {
+    const bool ylo = (BC == BC_CAVITY || (slab_walls & SLAB_LO_WALL)) && y == 0;
+    const bool yhi = (BC == BC_CAVITY || (slab_walls & SLAB_HI_WALL)) && y == ny - 1;
     if (x == 0 || x == nx - 1) {
       kind = (x == 0) ? 0 : 1;
       cx = (x == 0) ? 1 : nx - 2;
-      if (y == 0) cy = 1;
-      else if (y == ny - 1) cy = ny - 2;
-    } else if (y == 0 || y == ny - 1) {
+      if (ylo) cy = 1;
+      else if (yhi) cy = ny - 2;
+    } else if (ylo || yhi) {
       kind = 2;
-      cy = (y == 0) ? 1 : ny - 2;
+      cy = ylo ? 1 : ny - 2;
     }
   } else if (BC == BC_CHANNEL) {
     if (y == 0 || y == ny - 1) {
@@ -227,13 +228,16 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
                                               const uint32_t* __restrict__ tick_in,
                                               uint32_t* __restrict__ tick_out,
                                               const C* __restrict__ um_in,
-                                              C* __restrict__ um_out) {
+                                              C* __restrict__ um_out, const int slab_walls) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t tick = read_tick<S, C>(tick_in, tick_out);
   if (x >= nx || y >= ny) return;
+  if (BC == BC_SLAB && ((y == 0 && !(slab_walls & SLAB_LO_WALL)) ||
+                        (y == ny - 1 && !(slab_walls & SLAB_HI_WALL))))
+    return;  // a halo row: the neighbouring slab's values, read only
   step_node<S, C, BC>(src, dst, phi_field, mac, P, x, y, nx, ny, pitch, plane, scale, inv_scale,
-                      write_macros, tick, nullptr, um_in, um_out);
+                      write_macros, tick, nullptr, um_in, um_out, slab_walls);
 }
 
 // S_0 from the fields held in the macro planes (rho, ux, uy, Tf, Ts), then
@@ -290,19 +294,25 @@ cudaError_t launch_step_t(const LatticeArgs& a, const NodeParams<double>& Pd, St
     case BC_CAVITY:
       k_step<S, C, BC_CAVITY><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny, a.pitch,
                                                       a.plane, scale, inv_scale, a.write_macros,
-                                                      a.tick_in, a.tick_out, um_in, um_out);
+                                                      a.tick_in, a.tick_out, um_in, um_out, 0);
       break;
     case BC_PERIODIC:
       k_step<S, C, BC_PERIODIC><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
                                                         a.pitch, a.plane, scale, inv_scale,
                                                         a.write_macros, a.tick_in, a.tick_out,
-                                                        um_in, um_out);
+                                                        um_in, um_out, 0);
       break;
     case BC_CHANNEL:
       k_step<S, C, BC_CHANNEL><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
                                                        a.pitch, a.plane, scale, inv_scale,
                                                        a.write_macros, a.tick_in, a.tick_out,
-                                                       um_in, um_out);
+                                                       um_in, um_out, 0);
+      break;
+    case BC_SLAB:
+      k_step<S, C, BC_SLAB><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny, a.pitch,
+                                                    a.plane, scale, inv_scale, a.write_macros,
+                                                    a.tick_in, a.tick_out, um_in, um_out,
+                                                    a.slab_walls);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -91,6 +91,11 @@ SIGNATURES = {
     "ltne_set_schedule": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
     "ltne_get_schedule": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32)]),
+    "ltne_set_staging": (C.c_int, [_vp, C.c_int32]),
+    "ltne_slab_scratch_bytes": (C.c_size_t, [_vp, C.c_int32]),
+    "ltne_step_slabs": (C.c_int, [_vp, C.c_int32, C.c_int64, _vp, C.c_size_t]),
+    "ltne_check_bounded_wait": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32)]),
+    "ltne_get_staging": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "ltne_observables_static": (C.c_int, [C.POINTER(ltne_params), _vp, C.c_int64, _vp, C.c_int64,
                                           _vp, C.POINTER(ltne_obs)]),
     "ltne_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_int64, C.c_int32]),
@@ -231,6 +236,32 @@ def ltne_set_schedule(h, block_x, block_y, nodes_per_thread):
            "ltne_set_schedule")
 
 
+def ltne_set_staging(h, staged):
+    _check(_lib().ltne_set_staging(h, int(staged)), "ltne_set_staging")
+
+
+def ltne_slab_scratch_bytes(h, nslabs) -> int:
+    return int(_lib().ltne_slab_scratch_bytes(h, int(nslabs)))
+
+
+def ltne_step_slabs(h, nslabs, n, scratch_ptr, nbytes):
+    _check(_lib().ltne_step_slabs(h, int(nslabs), int(n), _vp(int(scratch_ptr)), int(nbytes)),
+           "ltne_step_slabs")
+
+
+def ltne_check_bounded_wait(stream_ptr, spins) -> int:
+    v = C.c_int32()
+    _check(_lib().ltne_check_bounded_wait(_vp(int(stream_ptr)), int(spins), C.byref(v)),
+           "ltne_check_bounded_wait")
+    return v.value
+
+
+def ltne_get_staging(h) -> int:
+    v = C.c_int32()
+    _check(_lib().ltne_get_staging(h, C.byref(v)), "ltne_get_staging")
+    return v.value
+
+
 def ltne_get_schedule(h):
     bx, by, npt = C.c_int32(), C.c_int32(), C.c_int32()
     _check(_lib().ltne_get_schedule(h, C.byref(bx), C.byref(by), C.byref(npt)),
@@ -331,6 +362,29 @@ class Cavity:
     @property
     def schedule(self):
         return ltne_get_schedule(self.h)
+
+    def step_slabs(self, nslabs, n):
+        """Advance n steps as nslabs row slabs with halo exchanges (the same
+        bits as step(n)); the slab buffers are a temporary torch tensor."""
+        import torch
+
+        nb = ltne_slab_scratch_bytes(self.h, nslabs)
+        if nb == 0:
+            raise LtneError(LTNE_ERR_INVALID_ARG, "ltne_slab_scratch_bytes")
+        buf = torch.empty(nb + 256, dtype=torch.uint8, device=self.workspace.device)
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        ltne_step_slabs(self.h, nslabs, n, ptr, nb)
+        self.stream.synchronize()  # the slab buffers are released on return
+        return self
+
+    def set_staging(self, staged):
+        """Step from TMA-staged shared-memory tiles (1) or direct loads (0)."""
+        ltne_set_staging(self.h, staged)
+        return self
+
+    @property
+    def staging(self):
+        return ltne_get_staging(self.h)
 
     def adjoint(self, porosity, n_steps, segment=None, rho=None, T_f=None, T_s=None):
         """Run n_steps from the given initial fields (fluid at rest) and return

@@ -180,4 +180,22 @@ def test_option_validation_without_gpu(lt):
             lt.LTNE_ERR_INVALID_ARG if storage == lt.LTNE_F64 else lt.LTNE_OK)
         assert lib.ltne_set_schedule(h, 256, 1, 1) == lt.LTNE_OK
         assert lt.ltne_get_schedule(h) == (256, 1, 1)
+        # staged tiles: float arithmetic and cavity walls only
+        assert lib.ltne_set_staging(h, 2) == lt.LTNE_ERR_INVALID_ARG
+        assert lib.ltne_set_staging(h, 1) == (
+            lt.LTNE_ERR_INVALID_ARG if storage == lt.LTNE_F64 else lt.LTNE_OK)
+        assert lt.ltne_get_staging(h) == (0 if storage == lt.LTNE_F64 else 1)
+        lt.ltne_destroy(h)
+        h = lt.ltne_create(lt.ltne_default_params(32, 32, storage=storage,
+                                                  bc=lt.LTNE_BC_PERIODIC))
+        assert lib.ltne_set_staging(h, 1) == lt.LTNE_ERR_INVALID_ARG
+        assert lt.ltne_slab_scratch_bytes(h, 2) == 0  # slabs: cavity walls only
+        lt.ltne_destroy(h)
+        # slabs: FP32 / FP64 cavities, at least two rows per slab
+        h = lt.ltne_create(lt.ltne_default_params(32, 20, storage=storage))
+        supported = storage in (lt.LTNE_F32, lt.LTNE_F64)
+        assert (lt.ltne_slab_scratch_bytes(h, 4) > 0) == supported
+        assert lt.ltne_slab_scratch_bytes(h, 11) == 0
+        assert lib.ltne_step_slabs(h, 2, 1, None, 0) in (
+            lt.LTNE_ERR_STATE if supported else lt.LTNE_ERR_INVALID_ARG,)
         lt.ltne_destroy(h)

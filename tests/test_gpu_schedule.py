@@ -137,3 +137,41 @@ def test_autotuner_picks_a_valid_schedule(storage):
     b = cavity_for(cfg, storage=storage).set_schedule(*best).set_fields().step(60).fields()
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+
+
+def _staged_pair(cfg, steps, storage, phi, staged):
+    c = cavity_for(cfg, storage=storage, phi=phi).set_schedule(64, 2, 2)
+    if staged:
+        c.set_staging(1)
+    return c.set_fields(porosity=phi).step(steps)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_staged_tiles_give_the_same_bits(storage):
+    """The two-node kernel fed from TMA-staged shared-memory tiles against
+    the direct two-node kernel: the same bits, on a ragged cavity (odd width,
+    partial tiles, walls), on one with more tiles than resident blocks (the
+    persistent loop reuses both stages many times) and with the local h_v
+    model and the correction term."""
+    cases = [(203, 77, {}, 61), (1100, 300, {}, 62),
+             (130, 67, dict(hv_local=1, Dp_over_L=0.0135, thermal_correction=1), 63)]
+    for nx, ny, extra, seed in cases:
+        cfg = dict(W.random_params(seed, nx, ny), **extra)
+        phi = W.porosity_field(nx, ny, 0.4, 0.9, seed=seed + 1).reshape(-1)
+        a = _staged_pair(cfg, 150, storage, phi, staged=False)
+        b = _staged_pair(cfg, 150, storage, phi, staged=True)
+        assert b.staging == 1
+        fa, fb = a.fields(), b.fields()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), (nx, ny, k)
+        assert b.observables()["nonfinite"] == 0
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    from paper_1608_04118_gb300.ltne import ltne_check_bounded_wait
+
+    s = torch.cuda.current_stream()
+    assert ltne_check_bounded_wait(s.cuda_stream, 5000) == 1
+    cfg = W.random_params(71, 300, 40)
+    c = cavity_for(cfg, storage="f16").set_staging(1).set_fields().step(40)
+    assert c.observables()["step"] == 40
