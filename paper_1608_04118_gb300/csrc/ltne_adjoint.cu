@@ -131,55 +131,90 @@ __global__ void __launch_bounds__(256) k_adj_seed(const C* __restrict__ SN, C* _
 
 // R1: fold the wall nodes' adjoints onto their interior neighbours.
 // Ring of interior nodes next to a wall: rows y = 1 and y = ny-2 (all
-// interior x), then columns x = 1 and x = nx-2 for 2 <= y <= ny-3.
+// interior x), then columns x = 1 and x = nx-2 for 2 <= y <= ny-3.  Four
+// lanes of a warp serve one ring node: lane k folds the k-th wall node whose
+// rebuild reads it (at most three: a side wall, a bottom/top wall and a
+// corner, which the isothermal columns own), the lanes' contributions are
+// summed in a fixed butterfly order, and lane 0 adds the sum to the node's
+// adjoint -- so a corner costs one transposed rebuild of latency, not three.
 template <typename C>
-__global__ void __launch_bounds__(256) k_adj_wall(C* __restrict__ lam,
+__device__ __forceinline__ C lane4_sum(C v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(128) k_adj_wall(C* __restrict__ lam,
                                                   const C* __restrict__ Snext,
                                                   const C* __restrict__ phi,
                                                   C* __restrict__ phib, C* __restrict__ hb,
                                                   const NodeParams<C> P, int nx, int ny,
                                                   int64_t pitch, int64_t plane) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = t >> 2, lane = t & 3;
   const int row = nx - 2, col = ny - 4;
-  int x, y;
-  if (t < row) { x = 1 + t; y = 1; }
-  else if (t < 2 * row) { x = 1 + t - row; y = ny - 2; }
-  else if (t < 2 * row + col) { x = 1; y = 2 + t - 2 * row; }
-  else if (t < 2 * row + 2 * col) { x = nx - 2; y = 2 + t - 2 * row - col; }
-  else return;
+  // every lane reaches the shuffles; lanes past the ring only contribute zeros
+  const bool valid = q < 2 * row + 2 * col;
+  int x = 1, y = 1;
+  if (q < row) { x = 1 + q; y = 1; }
+  else if (q < 2 * row) { x = 1 + q - row; y = ny - 2; }
+  else if (q < 2 * row + col) { x = 1; y = 2 + q - 2 * row; }
+  else if (valid) { x = nx - 2; y = 2 + q - 2 * row - col; }
   const int64_t off = (int64_t)y * pitch + x;
-  C L_f[9], L_gf[5], L_gs[5];
-  load19(lam, plane, off, L_f, L_gf, L_gs);
-  C f[9], gf[5], gs[5];
-  load19(Snext, plane, off, f, gf, gs);
-  const C ph = phi[off];
-  const Medium<C> md = medium_at<C>(P, ph);
-  MediumBar<C> mdb;
-  zero(mdb);
   // wall nodes whose rebuild reads this node (isothermal columns own the corners)
-  int wx[3], wy[3];
-  bool iso[3];
+  int wx[3] = {0, 0, 0}, wy[3] = {0, 0, 0};
+  bool iso[3] = {false, false, false};
   int nw = 0;
   if (x == 1) { wx[nw] = 0; wy[nw] = y; iso[nw] = true; ++nw; }
   if (x == nx - 2) { wx[nw] = nx - 1; wy[nw] = y; iso[nw] = true; ++nw; }
   if (y == 1) { wx[nw] = x; wy[nw] = 0; iso[nw] = false; ++nw; }
   if (y == ny - 2) { wx[nw] = x; wy[nw] = ny - 1; iso[nw] = false; ++nw; }
   const bool cx0 = (x == 1), cx1 = (x == nx - 2), cy0 = (y == 1), cy1 = (y == ny - 2);
-  int cwx[4], cwy[4], nc = 0;
-  if (cx0 && cy0) { cwx[nc] = 0; cwy[nc] = 0; ++nc; }
-  if (cx0 && cy1) { cwx[nc] = 0; cwy[nc] = ny - 1; ++nc; }
-  if (cx1 && cy0) { cwx[nc] = nx - 1; cwy[nc] = 0; ++nc; }
-  if (cx1 && cy1) { cwx[nc] = nx - 1; cwy[nc] = ny - 1; ++nc; }
-  const C zf[9] = {}, zg[5] = {};
-  for (int k = 0; k < nw + nc; ++k) {
-    const int bx = k < nw ? wx[k] : cwx[k - nw];
-    const int by = k < nw ? wy[k] : cwy[k - nw];
-    const bool isothermal = k < nw ? iso[k] : true;
-    const int64_t boff = (int64_t)by * pitch + bx;
+  if (cx0 && cy0 && nw < 3) { wx[nw] = 0; wy[nw] = 0; iso[nw] = true; ++nw; }
+  if (cx0 && cy1 && nw < 3) { wx[nw] = 0; wy[nw] = ny - 1; iso[nw] = true; ++nw; }
+  if (cx1 && cy0 && nw < 3) { wx[nw] = nx - 1; wy[nw] = 0; iso[nw] = true; ++nw; }
+  if (cx1 && cy1 && nw < 3) { wx[nw] = nx - 1; wy[nw] = ny - 1; iso[nw] = true; ++nw; }
+  C cf[9] = {}, cgf[5] = {}, cgs[5] = {};
+  MediumBar<C> mdb;
+  zero(mdb);
+  const C ph = valid ? phi[off] : C(0.5);
+  if (valid && lane < nw) {
+    C f[9], gf[5], gs[5];
+    load19(Snext, plane, off, f, gf, gs);
+    const Medium<C> md = medium_at<C>(P, ph);
+    const int64_t boff = (int64_t)wy[lane] * pitch + wx[lane];
     C lf[9], lgf[5], lgs[5];
     load19(lam, plane, boff, lf, lgf, lgs);
-    nee_adjoint<C>(P, md, f, gf, gs, isothermal, lf, lgf, lgs, L_f, L_gf, L_gs, mdb);
+    nee_adjoint<C>(P, md, f, gf, gs, iso[lane], lf, lgf, lgs, cf, cgf, cgs, mdb);
+    const C zf[9] = {}, zg[5] = {};
     store19(lam, plane, boff, zf, zg, zg);  // a wall node's pulled values are unused
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) cf[i] = lane4_sum(cf[i]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    cgf[i] = lane4_sum(cgf[i]);
+    cgs[i] = lane4_sum(cgs[i]);
+  }
+  mdb.phi = lane4_sum(mdb.phi);
+  mdb.inv_phi = lane4_sum(mdb.inv_phi);
+  mdb.a = lane4_sum(mdb.a);
+  mdb.b = lane4_sum(mdb.b);
+  mdb.inv_1d = lane4_sum(mdb.inv_1d);
+  mdb.c0 = lane4_sum(mdb.c0);
+  mdb.c1 = lane4_sum(mdb.c1);
+  mdb.l0 = lane4_sum(mdb.l0);
+  mdb.l1 = lane4_sum(mdb.l1);
+  if (!valid || lane != 0) return;
+  C L_f[9], L_gf[5], L_gs[5];
+  load19(lam, plane, off, L_f, L_gf, L_gs);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) L_f[i] += cf[i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    L_gf[i] += cgf[i];
+    L_gs[i] += cgs[i];
   }
   store19(lam, plane, off, L_f, L_gf, L_gs);
   C pb = C(0), hv = C(0);
@@ -471,8 +506,8 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
                                                           ny, pitch, plane, inv_dT);
     for (int64_t j = len - 1; j >= 0; --j) {
       if (ring > 0)
-        k_adj_wall<C><<<(ring + 127) / 128, 128, 0, s_>>>(lL, slot(j + 1), phi, phib, hb, P, nx,
-                                                          ny, pitch, plane);
+        k_adj_wall<C><<<(4 * ring + 127) / 128, 128, 0, s_>>>(lL, slot(j + 1), phi, phib, hb, P,
+                                                              nx, ny, pitch, plane);
       k_adj_main<C><<<grd, blk, 0, s_>>>(lL, lO, slot(j), phi, phib, hb, P, nx, ny, pitch,
                                          plane);
       C* t = lL;
