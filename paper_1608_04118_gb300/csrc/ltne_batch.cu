@@ -5,13 +5,14 @@
 // three-distribution MRT-LB method, arXiv:1608.04118).
 //
 // Work decomposition: every cavity is cut into tiles of TX x TY nodes; the
-// tile list (cavity, x0, y0) is built on the host for the schedule the
-// autotuner picked.  A block of TX*TY/NPT threads walks the list with a
-// stride of the grid size (round-robin, so block loads differ by at most one
-// tile), stages the tile's cavity constants in shared memory and updates
-// NPT = 1 node per thread, or NPT = 2 neighbouring nodes in paired FP32
-// arithmetic (the two-node step of ltne_pair.cuh).  FP32 storage and
-// arithmetic, uniform porosity per cavity.
+// tile list (cavity, origin and the cavity's geometry per tile) is built on
+// the host for the schedule the autotuner picked.  Either one block per tile
+// (k_batch_tile: the block reads its descriptor and the cavity constants
+// straight from global memory) or a persistent grid whose blocks walk the
+// list with a stride of the grid size, staging each tile's constants in
+// shared memory (k_batch_step).  A thread updates NPT = 1 node, or NPT = 2
+// neighbouring nodes in paired FP32 arithmetic (the two-node step of
+// ltne_pair.cuh).  FP32 storage and arithmetic, uniform porosity per cavity.
 #include <math.h>
 #include <string.h>
 
@@ -45,100 +46,77 @@ struct BatchCavity {
 
 static_assert(sizeof(NodeParams<float>) % sizeof(uint32_t) == 0, "NodeParams<float> layout");
 static_assert(sizeof(BatchConst) % sizeof(uint32_t) == 0, "BatchConst layout");
-// Words of constants staged per tile: the one-node step reads P only.
-template <int NPT>
-constexpr int const_words() {
-  return (int)((NPT == 1 ? sizeof(NodeParams<float>) : sizeof(BatchConst)) / sizeof(uint32_t));
-}
 constexpr int kMinBlockThreads = 64;  // every schedule has at least this many
 
-// What a tile needs of its cavity besides the constants.
-struct TileHead {
-  int nx, ny;
+// One tile of the list: its cavity, origin, and the cavity geometry a tile
+// needs (copied from the cavity table, so that a block reads one descriptor
+// and can issue its population loads without a dependent second lookup).
+struct TileDesc {
+  int32_t c, x0, y0, nx, ny, pad;
   int64_t pitch, plane, pop_off, mac_off;
 };
 
-__device__ __forceinline__ TileHead tile_head(const BatchCavity* __restrict__ cav, int c) {
-  return TileHead{cav[c].nx, cav[c].ny, cav[c].pitch, cav[c].plane, cav[c].pop_off,
-                  cav[c].mac_off};
+// The step of the nodes a thread owns in tile d: one node, or a pair of
+// neighbouring nodes (two-node step where both are off the side walls).
+template <int NPT>
+__device__ __forceinline__ void tile_nodes(const float* __restrict__ src, float* __restrict__ dst,
+                                           float* __restrict__ mac, const TileDesc& d,
+                                           const BatchConst& K, int lx, int ly,
+                                           int write_macros) {
+  const float* s = src + d.pop_off;
+  float* o = dst + d.pop_off;
+  float* m = mac + d.mac_off;
+  const int y = d.y0 + ly;
+  if constexpr (NPT == 1) {
+    const int x = d.x0 + lx;
+    if (x < d.nx && y < d.ny)
+      step_node<float, float, BC_CAVITY>(s, o, nullptr, m, K.P, x, y, d.nx, d.ny, d.pitch,
+                                         d.plane, 1.0f, 1.0f, write_macros, 0u);
+  } else {
+    const int x0 = d.x0 + 2 * lx;
+    if (x0 < d.nx && y < d.ny) {
+      if (x0 > 0 && x0 + 2 < d.nx) {
+        step_pair<float, BC_CAVITY>(s, o, nullptr, m, K.P2, x0, y, d.nx, d.ny,
+                                    (uint32_t)d.pitch, (uint32_t)d.plane, 1.0f, 1.0f,
+                                    write_macros, 0u, nullptr, nullptr);
+      } else {  // a wall node in the pair, or the last node of an odd row
+        step_node<float, float, BC_CAVITY>(s, o, nullptr, m, K.P, x0, y, d.nx, d.ny, d.pitch,
+                                           d.plane, 1.0f, 1.0f, write_macros, 0u);
+        if (x0 + 1 < d.nx)
+          step_node<float, float, BC_CAVITY>(s, o, nullptr, m, K.P, x0 + 1, y, d.nx, d.ny,
+                                             d.pitch, d.plane, 1.0f, 1.0f, write_macros, 0u);
+      }
+    }
+  }
 }
 
-// The descriptor, cavity header and constants of a block's next tile are
-// loaded while it works on the current one (constants double-buffered in
-// shared memory), so a tile's population loads start right after the
-// barrier that closes the previous tile.
-// Register budgets: 64 per thread for the one-node step (it fits without
-// spilling; left free, the tile pipeline takes 124), the pair kernel's for two.
+// One block per tile: the block reads its descriptor and takes the cavity
+// constants straight from the cavity table (uniform loads through the
+// read-only cache), with no staging and no barrier.
+template <int NPT>
+__global__ void __launch_bounds__(NPT == 1 ? 256 : kPairMaxThreads, NPT == 1 ? 4 : kPairMinBlocks)
+    k_batch_tile(const float* __restrict__ src, float* __restrict__ dst, float* __restrict__ mac,
+                 const BatchCavity* __restrict__ cav, const TileDesc* __restrict__ tiles,
+                 int tx_log2, int write_macros) {
+  const TileDesc d = tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  tile_nodes<NPT>(src, dst, mac, d, cav[d.c].K, tid & ((1 << tx_log2) - 1), tid >> tx_log2,
+                  write_macros);
+}
+
+// Persistent form: a grid of `blocks` blocks walks the tile list with a
+// stride of the grid size (round-robin, so block loads differ by at most
+// one tile), each tile exactly as in k_batch_tile.
 template <int NPT>
 __global__ void __launch_bounds__(NPT == 1 ? 256 : kPairMaxThreads, NPT == 1 ? 4 : kPairMinBlocks)
     k_batch_step(const float* __restrict__ src, float* __restrict__ dst, float* __restrict__ mac,
-                 const BatchCavity* __restrict__ cav, const int4* __restrict__ tiles, int ntiles,
-                 int tx_log2, int write_macros) {
-  constexpr int kWords = const_words<NPT>();
-  constexpr int kPer = (kWords + kMinBlockThreads - 1) / kMinBlockThreads;
-  __shared__ BatchConst sK[2];
-  const int tid = threadIdx.x, nthreads = blockDim.x;
+                 const BatchCavity* __restrict__ cav, const TileDesc* __restrict__ tiles,
+                 int ntiles, int tx_log2, int write_macros) {
+  const int tid = threadIdx.x;
   const int lx = tid & ((1 << tx_log2) - 1), ly = tid >> tx_log2;
-  auto words = [&](int c) { return reinterpret_cast<const uint32_t*>(&cav[c].K); };
-  int t = blockIdx.x;
-  if (t >= ntiles) return;
-  int4 tl = tiles[t];  // (cavity, x0, y0, -)
-  TileHead hd = tile_head(cav, tl.x);
-  for (int w = tid; w < kWords; w += nthreads)
-    reinterpret_cast<uint32_t*>(&sK[0])[w] = words(tl.x)[w];
-  __syncthreads();
-  int buf = 0;
-  for (; t < ntiles; t += gridDim.x) {
-    const int tn = t + gridDim.x;
-    int4 tl_next = tl;
-    TileHead hd_next = hd;
-    uint32_t word[kPer];
-    if (tn < ntiles) {
-      tl_next = tiles[tn];
-      hd_next = tile_head(cav, tl_next.x);
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        const int w = tid + k * nthreads;
-        word[k] = w < kWords ? words(tl_next.x)[w] : 0u;
-      }
-    }
-    const float* s = src + hd.pop_off;
-    float* d = dst + hd.pop_off;
-    float* m = mac + hd.mac_off;
-    const int y = tl.z + ly;
-    if constexpr (NPT == 1) {
-      const int x = tl.y + lx;
-      if (x < hd.nx && y < hd.ny)
-        step_node<float, float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P, x, y, hd.nx, hd.ny,
-                                           hd.pitch, hd.plane, 1.0f, 1.0f, write_macros, 0u);
-    } else {
-      const int x0 = tl.y + 2 * lx;
-      if (x0 < hd.nx && y < hd.ny) {
-        if (x0 > 0 && x0 + 2 < hd.nx) {
-          step_pair<float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P2, x0, y, hd.nx, hd.ny,
-                                      (uint32_t)hd.pitch, (uint32_t)hd.plane, 1.0f, 1.0f,
-                                      write_macros, 0u, nullptr, nullptr);
-        } else {  // a wall node in the pair, or the last node of an odd row
-          step_node<float, float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P, x0, y, hd.nx, hd.ny,
-                                             hd.pitch, hd.plane, 1.0f, 1.0f, write_macros, 0u);
-          if (x0 + 1 < hd.nx)
-            step_node<float, float, BC_CAVITY>(s, d, nullptr, m, sK[buf].P, x0 + 1, y, hd.nx,
-                                               hd.ny, hd.pitch, hd.plane, 1.0f, 1.0f,
-                                               write_macros, 0u);
-        }
-      }
-    }
-    if (tn < ntiles) {
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        const int w = tid + k * nthreads;
-        if (w < kWords) reinterpret_cast<uint32_t*>(&sK[buf ^ 1])[w] = word[k];
-      }
-    }
-    __syncthreads();  // sK[buf ^ 1] complete; nobody reads sK[buf] any more
-    buf ^= 1;
-    tl = tl_next;
-    hd = hd_next;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TileDesc d = tiles[t];
+    tile_nodes<NPT>(src, dst, mac, d, cav[d.c].K, lx, ly, write_macros);
   }
 }
 
@@ -206,14 +184,18 @@ void drop_graphs(ltne_batch* b) {
 }
 
 int upload_schedule(ltne_batch* b) {
-  std::vector<int4> tl;
+  std::vector<TileDesc> tl;
   tl.reserve((size_t)count_tiles(b, b->tx, b->ty));
-  for (int c = 0; c < b->count; ++c)
-    for (int y0 = 0; y0 < b->cav[c].ny; y0 += b->ty)
-      for (int x0 = 0; x0 < b->cav[c].nx; x0 += b->tx) tl.push_back(make_int4(c, x0, y0, 0));
+  for (int c = 0; c < b->count; ++c) {
+    const BatchCavity& cv = b->cav[c];
+    for (int y0 = 0; y0 < cv.ny; y0 += b->ty)
+      for (int x0 = 0; x0 < cv.nx; x0 += b->tx)
+        tl.push_back(TileDesc{c, x0, y0, cv.nx, cv.ny, 0, cv.pitch, cv.plane, cv.pop_off,
+                              cv.mac_off});
+  }
   b->ntiles = (int64_t)tl.size();
   if (b->ntiles > b->max_tiles) return LTNE_ERR_INVALID_ARG;
-  cudaError_t e = cudaMemcpyAsync(b->ws + b->off_tiles, tl.data(), tl.size() * sizeof(int4),
+  cudaError_t e = cudaMemcpyAsync(b->ws + b->off_tiles, tl.data(), tl.size() * sizeof(TileDesc),
                                   cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return fail_cuda(e);
@@ -233,13 +215,19 @@ cudaError_t launch_batch_step(ltne_batch* b, int src_buf, int write_macros, cuda
   float* dst = reinterpret_cast<float*>(b->ws + b->off_pop[src_buf ^ 1]);
   float* mac = reinterpret_cast<float*>(b->ws + b->off_mac);
   const BatchCavity* cav = reinterpret_cast<const BatchCavity*>(b->ws + b->off_cav);
-  const int4* tiles = reinterpret_cast<const int4*>(b->ws + b->off_tiles);
-  if (b->npt == 2)
+  const TileDesc* tiles = reinterpret_cast<const TileDesc*>(b->ws + b->off_tiles);
+  if (b->blocks == 0) {  // one block per tile
+    if (b->npt == 2)
+      k_batch_tile<2><<<grid, threads, 0, st>>>(src, dst, mac, cav, tiles, tx_log2, write_macros);
+    else
+      k_batch_tile<1><<<grid, threads, 0, st>>>(src, dst, mac, cav, tiles, tx_log2, write_macros);
+  } else if (b->npt == 2) {
     k_batch_step<2><<<grid, threads, 0, st>>>(src, dst, mac, cav, tiles, (int)b->ntiles, tx_log2,
                                               write_macros);
-  else
+  } else {
     k_batch_step<1><<<grid, threads, 0, st>>>(src, dst, mac, cav, tiles, (int)b->ntiles, tx_log2,
                                               write_macros);
+  }
   return cudaGetLastError();
 }
 
@@ -343,7 +331,7 @@ int ltne_batch_create(const ltne_params* params, int32_t count, void* cuda_strea
   b->off_cav = off;
   off = align_up(off + (size_t)count * sizeof(BatchCavity), A);
   b->off_tiles = off;
-  off = align_up(off + (size_t)b->max_tiles * sizeof(int4), A);
+  off = align_up(off + (size_t)b->max_tiles * sizeof(TileDesc), A);
   b->ws_bytes = off;
   *out = b;
   return LTNE_OK;
