@@ -98,5 +98,9 @@ int derive_params(const ltne_params& p, const double* porosity, NodeParams<doubl
 int finish_observables(const ltne_params& p, const DerivedInfo& info, int64_t step,
                        bool have_prev, const double* acc, ltne_obs* out);
 int reduce_blocks(int nx, int ny);  // pass-1 blocks (= partial vectors)
+// Pass-1 blocks stay within this count whenever rows of 64 allow it (every
+// lattice up to 8192 x 8192): the size of the fixed partials array of the
+// allocation-free observables.
+constexpr int kReduceMaxBlocks = 4096;
 
 }  // namespace ltne

@@ -4,11 +4,13 @@
 //
 // Two passes with a fixed summation order, so results are bitwise
 // reproducible for a given lattice size: pass 1 writes one partial vector per
-// block (RB columns x SEG rows) into a scratch buffer; pass 2 (one block)
+// block (RB columns x seg rows) into a scratch buffer; pass 2 (one block)
 // reduces the partials in block order.  Per-node terms are accumulated in
-// the fields' precision over at most SEG nodes per thread (FP64 on GB300
-// runs at a small fraction of the FP32 rate, so FP64 per node would make
-// this pass compute-bound); every combination above that is FP64.
+// the fields' precision over at most seg nodes per thread and across the 32
+// threads of a warp (FP64 on GB300 runs at a small fraction of the FP32
+// rate, so FP64 per node -- or a warp shuffle tree in FP64 in every block --
+// would make this pass compute-bound); every combination above that, the
+// warps of a block and the blocks, is FP64.
 #include "ltne_internal.h"
 
 namespace ltne {
@@ -16,10 +18,22 @@ namespace ltne {
 namespace {
 
 constexpr int RB = 256;  // threads per block in both passes
-constexpr int SEG = 64;  // rows per pass-1 block
+// Rows per pass-1 block: the smallest of 16, 32, 64 that keeps the block
+// count within kReduceMaxBlocks (more, shorter blocks keep more loads in
+// flight: 2048^2 with 64 rows gives 256 blocks, fewer than two per SM).
+int reduce_seg(int nx, int ny) {
+  const int cols = (nx + RB - 1) / RB;
+  for (int seg = 16; seg < 64; seg *= 2)
+    if ((int64_t)cols * ((ny + seg - 1) / seg) <= kReduceMaxBlocks) return seg;
+  return 64;
+}
 
-__device__ __forceinline__ double combine(int k, double a, double b) {
-  return (k == A_MAXU || k == A_MAXDT) ? fmax(a, b) : a + b;
+__device__ __forceinline__ float cmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double cmax(double a, double b) { return fmax(a, b); }
+
+template <typename C>
+__device__ __forceinline__ C combine(int k, C a, C b) {
+  return (k == A_MAXU || k == A_MAXDT) ? cmax(a, b) : a + b;
 }
 
 // Block-wide reduction of NACC accumulators per thread into acc of
@@ -30,7 +44,8 @@ __device__ void block_reduce(double (&acc)[NACC], double* sh /* [RB/32][NACC] */
   for (int k = 0; k < NACC; ++k) {
     double v = acc[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = combine(k, v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1)
+      v = combine<double>(k, v, __shfl_down_sync(0xffffffffu, v, o));
     acc[k] = v;
   }
   if (lane == 0)
@@ -40,19 +55,19 @@ __device__ void block_reduce(double (&acc)[NACC], double* sh /* [RB/32][NACC] */
   if (threadIdx.x == 0) {
     for (int w = 1; w < RB / 32; ++w)
 #pragma unroll
-      for (int k = 0; k < NACC; ++k) acc[k] = combine(k, acc[k], sh[w * NACC + k]);
+      for (int k = 0; k < NACC; ++k) acc[k] = combine<double>(k, acc[k], sh[w * NACC + k]);
   }
 }
 
-// Pass 1.  Block (RB threads) covers RB consecutive columns and SEG rows;
+// Pass 1.  Block (RB threads) covers RB consecutive columns and seg rows;
 // each thread walks its column down the segment (coalesced rows across the
-// warp), accumulating in the fields' own precision C over at most SEG nodes,
-// then everything from the per-thread partials upward is combined in FP64.
+// warp), accumulating in the fields' own precision C over at most seg nodes
+// and across the warp, then the warp partials and everything above in FP64.
 // Rows go in groups of RU (4 in FP32, 2 in FP64, which holds twice the
 // registers per value): all loads of a group are issued before any of its
 // snapshot stores, so a thread keeps RU rows of loads in flight.
 template <typename C>
-__global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a) {
+__global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
   constexpr int RU = sizeof(C) == 4 ? 4 : 2;
   __shared__ double sh[(RB / 32) * NACC];
   C acc[NACC];
@@ -63,8 +78,8 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a) {
   C* __restrict__ prev = static_cast<C*>(a.prev);
   const int64_t pl = a.plane;
   const int x = blockIdx.x * RB + threadIdx.x;
-  const int y0 = blockIdx.y * SEG;
-  const int y1 = min(y0 + SEG, a.ny);
+  const int y0 = blockIdx.y * seg;
+  const int y1 = min(y0 + seg, a.ny);
   const C phi_u = C(a.phi_u), sigma = C(a.sigma);
   // Wall-flux stencil weights: q_hot = 1.5 T_h - 2 T(1,y) + 0.5 T(2,y),
   // q_cold = -1.5 T_c + 2 T(nx-2,y) - 0.5 T(nx-3,y), trapezoid rule in y.
@@ -134,11 +149,27 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a) {
       }
     }
   }
-  double dacc[NACC];
+  // the warp in the fields' precision (fixed shuffle order), then the warp
+  // partials in FP64 in warp order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < NACC; ++k) dacc[k] = (double)acc[k];
-  block_reduce(dacc, sh);
+  for (int k = 0; k < NACC; ++k) {
+    C v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = combine<C>(k, v, __shfl_down_sync(0xffffffffu, v, o));
+    acc[k] = v;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) sh[warp * NACC + k] = (double)acc[k];
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double dacc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) dacc[k] = sh[k];
+    for (int w = 1; w < RB / 32; ++w)
+#pragma unroll
+      for (int k = 0; k < NACC; ++k) dacc[k] = combine<double>(k, dacc[k], sh[w * NACC + k]);
     const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int k = 0; k < NACC; ++k) a.partials[b * NACC + k] = dacc[k];
@@ -153,7 +184,8 @@ __global__ void __launch_bounds__(RB) k_reduce_pass2(const double* __restrict__ 
   for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
   for (int b = threadIdx.x; b < blocks; b += RB)
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) acc[k] = combine(k, acc[k], partials[(int64_t)b * NACC + k]);
+    for (int k = 0; k < NACC; ++k)
+      acc[k] = combine<double>(k, acc[k], partials[(int64_t)b * NACC + k]);
   block_reduce(acc, sh);
   if (threadIdx.x == 0)
 #pragma unroll
@@ -163,16 +195,18 @@ __global__ void __launch_bounds__(RB) k_reduce_pass2(const double* __restrict__ 
 }  // namespace
 
 int reduce_blocks(int nx, int ny) {
-  return ((nx + RB - 1) / RB) * ((ny + SEG - 1) / SEG);
+  const int seg = reduce_seg(nx, ny);
+  return ((nx + RB - 1) / RB) * ((ny + seg - 1) / seg);
 }
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
-  dim3 grid((a.nx + RB - 1) / RB, (a.ny + SEG - 1) / SEG);
+  const int seg = reduce_seg(a.nx, a.ny);
+  dim3 grid((a.nx + RB - 1) / RB, (a.ny + seg - 1) / seg);
   if ((int)(grid.x * grid.y) != a.blocks) return cudaErrorInvalidValue;
   if (a.is_double)
-    k_reduce_pass1<double><<<grid, RB, 0, st>>>(a);
+    k_reduce_pass1<double><<<grid, RB, 0, st>>>(a, seg);
   else
-    k_reduce_pass1<float><<<grid, RB, 0, st>>>(a);
+    k_reduce_pass1<float><<<grid, RB, 0, st>>>(a, seg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_pass2<<<1, RB, 0, st>>>(a.partials, a.blocks, a.out);

@@ -18,9 +18,9 @@ using namespace ltne;
 
 namespace {
 
-// Largest pass-1 grid served: 4096 blocks of 256 columns x 64 rows, i.e. any
-// lattice with ceil(nx/256) * ceil(ny/64) <= 4096 (8192 x 8192 fits).
-constexpr int kMaxBlocks = 4096;
+// Largest pass-1 grid served: 4096 blocks of 256 columns x 16 to 64 rows,
+// i.e. any lattice with ceil(nx/256) * ceil(ny/64) <= 4096 (8192 x 8192 fits).
+constexpr int kMaxBlocks = kReduceMaxBlocks;
 
 // Reduction scratch: kMaxBlocks partial vectors, then one result vector.
 // 4097 x 18 doubles = 590 KB, held by every GPU that loads the library.
