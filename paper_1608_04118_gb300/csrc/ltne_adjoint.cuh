@@ -54,9 +54,9 @@ LTNE_HD void medium_adjoint(const NodeParams<C>& P, C phi, const MediumBar<C>& m
   const C b_b = mb.b + C(0.5) * t_b;
   // a = hcoef / phi, b = hcoef / ((1 - phi) sigma)
   const C om = C(1) - phi;
-  hcoef_b += a_b * md.inv_phi + b_b / (om * P.sigma);
+  hcoef_b += a_b * md.inv_phi + b_b * md.inv_oms;
   C ip_b = mb.inv_phi + a_b * P.hcoef;
-  pb += b_b * P.hcoef / (om * om * P.sigma);
+  pb += b_b * P.hcoef * md.inv_oms * rcp_<C>(om);
   // c0(phi), c1(phi)
   const C ip = md.inv_phi;
   C dc0 = C(0), dc1 = C(0);
@@ -125,14 +125,15 @@ LTNE_HD void macros_adjoint(const NodeParams<C>& P, const Medium<C>& md, const C
   // den = l0 + R, R = sqrt(l0^2 + l1 |v|)
   mdb.l0 += den_b;
   if (R > C(0)) {
-    const C hR = den_b / (C(2) * R);
+    const C hR = C(0.5) * den_b * rcp_<C>(R);
     mdb.l0 += hR * C(2) * md.l0;
     mdb.l1 += hR * vmag;
     vmag_b += hR * md.l1;
   }
   if (vmag > C(0)) {
-    vx_b += vmag_b * vx / vmag;
-    vy_b += vmag_b * vy / vmag;
+    const C ivm = rcp_<C>(vmag);
+    vx_b += vmag_b * vx * ivm;
+    vy_b += vmag_b * vy * ivm;
   }
   // v = j / rho + phi G / 2
   C jx_b = in.jx + vx_b * ir;
@@ -196,13 +197,14 @@ LTNE_HD void collide_adjoint(const NodeParams<C>& P, const Medium<C>& md, const 
   const C sd = (A[5] + A[6]) + (A[7] + A[8]);
   const C ax = (A[5] - A[6]) + (A[8] - A[7]);
   const C ay = (A[5] - A[7]) + (A[6] - A[8]);
-  const C msb0 = (A[0] + sa + sd) / C(9);
-  const C msb1 = (C(-4) * A[0] - sa + C(2) * sd) / C(36);
-  const C msb2 = (C(4) * A[0] - C(2) * sa + sd) / C(36);
-  const C msb3 = ((A[1] - A[3]) + ax) / C(6);
-  const C msb4 = (C(-2) * (A[1] - A[3]) + ax) / C(12);
-  const C msb5 = ((A[2] - A[4]) + ay) / C(6);
-  const C msb6 = (C(-2) * (A[2] - A[4]) + ay) / C(12);
+  // divisions by the small integers of D as in the forward collision
+  const C msb0 = div_small<C>(A[0] + sa + sd, C(9), C(1.0 / 9.0));
+  const C msb1 = div_small<C>(C(-4) * A[0] - sa + C(2) * sd, C(36), C(1.0 / 36.0));
+  const C msb2 = div_small<C>(C(4) * A[0] - C(2) * sa + sd, C(36), C(1.0 / 36.0));
+  const C msb3 = div_small<C>((A[1] - A[3]) + ax, C(6), C(1.0 / 6.0));
+  const C msb4 = div_small<C>(C(-2) * (A[1] - A[3]) + ax, C(12), C(1.0 / 12.0));
+  const C msb5 = div_small<C>((A[2] - A[4]) + ay, C(6), C(1.0 / 6.0));
+  const C msb6 = div_small<C>(C(-2) * (A[2] - A[4]) + ay, C(12), C(1.0 / 12.0));
   const C msb7 = ((A[1] - A[2]) + (A[3] - A[4])) * C(0.25);
   const C msb8 = ((A[5] - A[6]) + (A[7] - A[8])) * C(0.25);
 
@@ -265,10 +267,10 @@ LTNE_HD void collide_adjoint(const NodeParams<C>& P, const Medium<C>& md, const 
   // ---- temperatures.  ns_b = D_N^-1 N go_b.
   {
     const C* B = gfo_b;
-    const C nb0 = ((B[0] + B[1]) + (B[2] + B[3]) + B[4]) / C(5);
+    const C nb0 = div_small<C>((B[0] + B[1]) + (B[2] + B[3]) + B[4], C(5), C(0.2));
     const C nb1 = (B[1] - B[3]) * C(0.5);
     const C nb2 = (B[2] - B[4]) * C(0.5);
-    const C nb3 = (C(-4) * B[0] + ((B[1] + B[2]) + (B[3] + B[4]))) / C(20);
+    const C nb3 = div_small<C>(C(-4) * B[0] + ((B[1] + B[2]) + (B[3] + B[4])), C(20), C(0.05));
     const C nb4 = ((B[1] - B[2]) + (B[3] - B[4])) * C(0.25);
     const C Tf = P.T0 + m.dTf;
     mb.sgf += nb0;
@@ -298,10 +300,10 @@ LTNE_HD void collide_adjoint(const NodeParams<C>& P, const Medium<C>& md, const 
   }
   {
     const C* B = gso_b;
-    const C nb0 = ((B[0] + B[1]) + (B[2] + B[3]) + B[4]) / C(5);
+    const C nb0 = div_small<C>((B[0] + B[1]) + (B[2] + B[3]) + B[4], C(5), C(0.2));
     const C nb1 = (B[1] - B[3]) * C(0.5);
     const C nb2 = (B[2] - B[4]) * C(0.5);
-    const C nb3 = (C(-4) * B[0] + ((B[1] + B[2]) + (B[3] + B[4]))) / C(20);
+    const C nb3 = div_small<C>(C(-4) * B[0] + ((B[1] + B[2]) + (B[3] + B[4])), C(20), C(0.05));
     const C nb4 = ((B[1] - B[2]) + (B[3] - B[4])) * C(0.25);
     mb.sgs += nb0;
     mb.Srs += nb0;
