@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_adj_seed(const C* __restrict__ SN, C* _
   macros_adjoint<C>(P, md, f, gf, gs, mb, fb, gfb, gsb, mdb);
   store19(lam, plane, off, fb, gfb, gsb);
   C pb = C(0), hv = C(0);
-  medium_adjoint<C>(P, ph, mdb, pb, hv);
+  medium_adjoint<C>(P, ph, md, mdb, pb, hv);
   phib[off] += pb;
   hb[off] += hv;
 }
@@ -179,10 +179,14 @@ __global__ void __launch_bounds__(128) k_adj_wall(C* __restrict__ lam,
   MediumBar<C> mdb;
   zero(mdb);
   const C ph = valid ? phi[off] : C(0.5);
+  const Medium<C> md = medium_at<C>(P, ph);
+  // lane 0 owns the ring node's adjoint: its load goes out first (no wall
+  // node store of this kernel touches it)
+  C L_f[9], L_gf[5], L_gs[5];
+  if (valid && lane == 0) load19(lam, plane, off, L_f, L_gf, L_gs);
   if (valid && lane < nw) {
     C f[9], gf[5], gs[5];
     load19(Snext, plane, off, f, gf, gs);
-    const Medium<C> md = medium_at<C>(P, ph);
     const int64_t boff = (int64_t)wy[lane] * pitch + wx[lane];
     C lf[9], lgf[5], lgs[5];
     load19(lam, plane, boff, lf, lgf, lgs);
@@ -207,8 +211,6 @@ __global__ void __launch_bounds__(128) k_adj_wall(C* __restrict__ lam,
   mdb.l0 = lane4_sum(mdb.l0);
   mdb.l1 = lane4_sum(mdb.l1);
   if (!valid || lane != 0) return;
-  C L_f[9], L_gf[5], L_gs[5];
-  load19(lam, plane, off, L_f, L_gf, L_gs);
 #pragma unroll
   for (int i = 0; i < 9; ++i) L_f[i] += cf[i];
 #pragma unroll
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(128) k_adj_wall(C* __restrict__ lam,
   }
   store19(lam, plane, off, L_f, L_gf, L_gs);
   C pb = C(0), hv = C(0);
-  medium_adjoint<C>(P, ph, mdb, pb, hv);
+  medium_adjoint<C>(P, ph, md, mdb, pb, hv);
   phib[off] += pb;
   hb[off] += hv;
 }
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(256) k_adj_main(const C* __restrict__ Lam,
   collide_adjoint<C>(P, md, f, gf, gs, qf, qgf, qgs, fb, gfb, gsb, mdb);
   store19(lam_out, plane, off, fb, gfb, gsb);
   C pb = C(0), hv = C(0);
-  medium_adjoint<C>(P, ph, mdb, pb, hv);
+  medium_adjoint<C>(P, ph, md, mdb, pb, hv);
   phib[off] += pb;
   hb[off] += hv;
 }

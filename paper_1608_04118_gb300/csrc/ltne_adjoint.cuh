@@ -38,10 +38,10 @@ LTNE_HD void zero(MediumBar<C>& b) {
 }
 
 // Medium coefficients -> (phi_b, hcoef_b).  Forward: medium_at().
+// md: the node's coefficients, medium_at(P, phi).
 template <typename C>
-LTNE_HD void medium_adjoint(const NodeParams<C>& P, C phi, const MediumBar<C>& mb, C& phi_b,
-                            C& hcoef_b) {
-  const Medium<C> md = medium_at<C>(P, phi);
+LTNE_HD void medium_adjoint(const NodeParams<C>& P, C phi, const Medium<C>& md,
+                            const MediumBar<C>& mb, C& phi_b, C& hcoef_b) {
   C pb = mb.phi;
   // l0 = (1 + phi c0 / 2) / 2, l1 = phi c1 / 2
   pb += mb.l0 * C(0.25) * md.c0;
