@@ -454,6 +454,19 @@ def run_adjoint(args):
 
     # context: the same physics on a 1024^2 lattice (1000 steps), where a
     # step is several waves of blocks rather than one latency-bound wave
+    def adjoint_mlups(n, k, sched):
+        ph = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+        cv = Cavity(n, n, stream=stream, storage="f32", permeability=LTNE_K_ERGUN,
+                    porosity_field=1, **kw).set_adjoint_schedule(sched)
+        sg = int(math.ceil(math.sqrt(k)))
+        cv.adjoint(ph, 2 * sg, segment=sg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cv.adjoint(ph, k, segment=sg)
+        torch.cuda.synchronize()
+        cv.close()
+        return n * n * k / (time.perf_counter() - t0) / 1e6
+
     def at_size(n, k):
         ph = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
         cv = Cavity(n, n, stream=stream, storage="f32", permeability=LTNE_K_ERGUN,
@@ -479,6 +492,11 @@ def run_adjoint(args):
                 "plain_forward_mlups": n * n * k / tf / 1e6, "ratio_to_plain_forward": tf / ta}
 
     big = None if args.no_context else at_size(1024, 1000)
+    # the two register budgets of the transposed collision (the default
+    # picks by lattice size)
+    forms = None if args.no_context else {
+        "%dx%d" % (m, m): {"one_wave": adjoint_mlups(m, k, 1), "capped": adjoint_mlups(m, k, 2)}
+        for m, k in ((nx, steps), (1024, 1000))}
     line = {"metric": "MLUPS (forward + adjoint, %dx%d)" % (nx, ny),
             "value": nodes * steps / t_adj / 1e6,
             "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
@@ -490,7 +508,7 @@ def run_adjoint(args):
             "seconds": t_adj, "plain_forward_mlups": nodes * steps / t_fwd / 1e6,
             "ratio_to_plain_forward": (nodes * steps / t_adj) / (nodes * steps / t_fwd),
             "J": J, "dJ_dH": dH, "max_abs_dJ_dphi": float(g.abs().max()),
-            "same_physics_1024": big}
+            "same_physics_1024": big, "register_budgets_mlups": forms}
     print(json.dumps(line), flush=True)
 
 

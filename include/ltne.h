@@ -271,6 +271,23 @@ int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
    (ceil(n_steps/segment) + segment + 4) * 19 planes of the compute type. */
 size_t ltne_adjoint_workspace_bytes(const ltne_handle* h, int64_t n_steps, int32_t segment);
 
+/* Register budget of the adjoint's transposed-collision kernel (no
+   counterpart in the paper).  LTNE_ADJ_ONE_WAVE: every register the kernel
+   wants (119 per thread in FP32), for lattices whose grid fits one wave of
+   the device, where a reverse step's time is one thread's latency;
+   LTNE_ADJ_CAPPED: registers capped so that four blocks of 256 threads
+   share an SM (FP32; a few values spill to local memory), for larger
+   lattices, where occupancy hides the latency.  LTNE_ADJ_AUTO (default)
+   picks by the lattice size.  The two builds run the same code; they agree
+   to rounding (under the cap the compiler may contract a different set of
+   multiply-adds), and each is deterministic.  LTNE_ERR_INVALID_ARG for
+   other values. */
+#define LTNE_ADJ_AUTO 0
+#define LTNE_ADJ_ONE_WAVE 1
+#define LTNE_ADJ_CAPPED 2
+int ltne_set_adjoint_schedule(ltne_handle* h, int32_t mode);
+int ltne_get_adjoint_schedule(const ltne_handle* h, int32_t* mode);
+
 /* Set the initial fields (as ltne_set_fields with u = 0; rho, T_f, T_s may
    be NULL), run n_steps >= 1 steps forward (the handle ends at step
    n_steps, exactly as after ltne_step), compute *J, and by the reverse

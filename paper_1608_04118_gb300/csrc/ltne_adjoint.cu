@@ -8,15 +8,20 @@
 // per-node collision (Eqs. 10, 32, 33 with Eqs. 5-7, 15, 37-46), Pull the
 // streaming (Eqs. 11, 34, 35) and W the wall rebuild.  Its transpose, applied
 // to the adjoint lambda_{n+1} of S_{n+1}:
-//   R1 (ring kernel): every wall node's adjoint is folded onto its interior
-//      neighbour through the transposed wall-rebuild Jacobian, then zeroed;
-//      one thread per neighbour (each wall node has exactly one), no atomics.
+//   R1 (wall fold): a wall node's populations are rebuilt from those of one
+//      interior neighbour r by non-equilibrium extrapolation; the transposed rebuild Jacobian at r
+//      maps the wall node's adjoint onto r.  The thread that computes a wall
+//      node's adjoint applies it at once and stores the result in the wall
+//      node's place (a wall node's own adjoint is never pulled).
 //   R2 (grid kernel): the adjoint of Coll's output at y is gathered from
 //      y + e_i (the transpose of a pull is a pull the other way; only
-//      interior targets pulled), then the transposed collision Jacobian at
+//      interior targets pulled; a target next to a wall adds the folds of its
+//      wall nodes in a fixed order), then the transposed collision Jacobian at
 //      S_n(y) gives lambda_n(y) and the porosity / h_v contributions.
 // Gradients accumulate per node (porosity, and the h_v term reduced once in
-// FP64 at the end), so the result is deterministic.
+// FP64 at the end; a fold's porosity term in its wall node's place of a
+// separate plane, added to r once at the end), so the result is
+// deterministic.
 //
 // Memory: sqrt(T)-style checkpointing.  The forward pass records S_a at the
 // start of every segment of K steps; the reverse sweep recomputes each
@@ -36,6 +41,18 @@ using namespace ltne;
 namespace {
 
 constexpr int kRB = 256;
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation is scheduled as its predecessor's blocks exit, before that
+// grid's completion is signalled; it waits here for the completion (and the
+// memory flush) before touching global memory.  Without the launch attribute
+// the wait is a no-op.  Every thread of every kernel below waits before any
+// global access or early return, so each grid completes only after its
+// predecessor did and the chain stays ordered.  No kernel triggers its
+// successor early (griddepcontrol.launch_dependents): at 256 x 256 an early
+// trigger, before or after the wait, made the whole adjoint 6-20% slower,
+// the wait alone 3% faster than plain stream order.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename C>
 __device__ __forceinline__ void load19(const C* __restrict__ b, int64_t plane, int64_t off,
@@ -68,6 +85,7 @@ __global__ void __launch_bounds__(256) k_step_record(const C* __restrict__ src,
                                                      int nx, int ny, int64_t pitch,
                                                      int64_t plane, int write_macros,
                                                      C* __restrict__ pre_out) {
+  chain_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -82,6 +100,7 @@ __global__ void __launch_bounds__(256) k_collide_pre(const C* __restrict__ pre,
                                                      const C* __restrict__ phi,
                                                      const NodeParams<C> P, int nx, int ny,
                                                      int64_t pitch, int64_t plane) {
+  chain_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -95,14 +114,102 @@ __global__ void __launch_bounds__(256) k_collide_pre(const C* __restrict__ pre,
   store19(dst, plane, off, f, gf, gs);
 }
 
+// R1 for a wall node: the interior node r its populations are rebuilt from
+// (the isothermal columns own the corners) and that node's state.
+template <typename C>
+struct WallSource {
+  C f[9], gf[5], gs[5];
+  C phi;
+  bool iso;
+};
+
+template <typename C>
+__device__ __forceinline__ void load_wall_source(const C* __restrict__ S,
+                                                 const C* __restrict__ phi, int x, int y, int nx,
+                                                 int ny, int64_t pitch, int64_t plane,
+                                                 WallSource<C>& w) {
+  int rx = x, ry;
+  if (x == 0 || x == nx - 1) {
+    rx = (x == 0) ? 1 : nx - 2;
+    ry = y < 1 ? 1 : (y > ny - 2 ? ny - 2 : y);
+    w.iso = true;
+  } else {
+    ry = (y == 0) ? 1 : ny - 2;
+    w.iso = false;
+  }
+  const int64_t roff = (int64_t)ry * pitch + rx;
+  load19(S, plane, roff, w.f, w.gf, w.gs);
+  w.phi = phi[roff];
+}
+
+// The wall node's adjoint (lf, lgf, lgs) through the transposed rebuild
+// Jacobian at r: stored in the wall node's place of lam; the porosity term
+// (for r) accumulates in the wall node's place of wphib, the h_v term in hv.
+template <typename C>
+__device__ __forceinline__ void fold_wall(const NodeParams<C>& P, const WallSource<C>& w,
+                                          const C (&lf)[9], const C (&lgf)[5], const C (&lgs)[5],
+                                          C* __restrict__ lam, C* __restrict__ wphib,
+                                          int64_t plane, int64_t off, C& hv) {
+  const Medium<C> md = medium_at<C>(P, w.phi);
+  C cf[9] = {}, cgf[5] = {}, cgs[5] = {};
+  MediumBar<C> mdb;
+  zero(mdb);
+  nee_adjoint<C>(P, md, w.f, w.gf, w.gs, w.iso, lf, lgf, lgs, cf, cgf, cgs, mdb);
+  store19(lam, plane, off, cf, cgf, cgs);
+  C pb = C(0), hb = C(0);
+  medium_adjoint<C>(P, w.phi, md, mdb, pb, hb);
+  wphib[off] += pb;
+  hv += hb;
+}
+
+// Adds to the gathered adjoint q (pulled from y + e_i) the folds stored at
+// the wall nodes of each target next to a wall: its side-column node, its
+// bottom/top-row node, then the corner, in that order.
+template <typename C>
+__device__ __forceinline__ void add_wall_folds(const C* __restrict__ Lam, int x, int y, int nx,
+                                               int ny, int64_t pitch, int64_t plane,
+                                               C (&qf)[9], C (&qgf)[5], C (&qgs)[5]) {
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int tx = x + ex[i], ty = y + ey[i];
+    if (tx < 1 || tx > nx - 2 || ty < 1 || ty > ny - 2) continue;
+    const bool cx = tx == 1 || tx == nx - 2, cy = ty == 1 || ty == ny - 2;
+    if (!cx && !cy) continue;
+    const int wx = (tx == 1) ? 0 : nx - 1, wy = (ty == 1) ? 0 : ny - 1;
+    int64_t wo[3];
+    bool wv[3];
+    wv[0] = cx;
+    wo[0] = (int64_t)ty * pitch + wx;
+    wv[1] = cy;
+    wo[1] = (int64_t)wy * pitch + tx;
+    wv[2] = cx && cy;
+    wo[2] = (int64_t)wy * pitch + wx;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (!wv[k]) continue;
+      qf[i] += Lam[(int64_t)i * plane + wo[k]];
+      if (i < 5) {
+        qgf[i] += Lam[(int64_t)(9 + i) * plane + wo[k]];
+        qgs[i] += Lam[(int64_t)(14 + i) * plane + wo[k]];
+      }
+    }
+  }
+}
+
 // lambda_N: J depends on S_N through the temperatures of columns 1 and 2
-// (wall-flux stencil of the Nusselt numbers, trapezoid weights in y).
+// (wall-flux stencil of the Nusselt numbers, trapezoid weights in y).  The
+// end nodes of the two columns lie on the bottom and top walls: their
+// adjoints are folded (R1) at once.
 template <typename C>
 __global__ void __launch_bounds__(256) k_adj_seed(const C* __restrict__ SN, C* __restrict__ lam,
                                                   const C* __restrict__ phi,
                                                   C* __restrict__ phib, C* __restrict__ hb,
-                                                  const NodeParams<C> P, int nx, int ny,
-                                                  int64_t pitch, int64_t plane, C inv_dT) {
+                                                  C* __restrict__ wphib, const NodeParams<C> P,
+                                                  int nx, int ny, int64_t pitch, int64_t plane,
+                                                  C inv_dT) {
+  chain_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * ny) return;
   const int y = t >> 1, x = 1 + (t & 1);
@@ -122,118 +229,38 @@ __global__ void __launch_bounds__(256) k_adj_seed(const C* __restrict__ SN, C* _
   MediumBar<C> mdb;
   zero(mdb);
   macros_adjoint<C>(P, md, f, gf, gs, mb, fb, gfb, gsb, mdb);
-  store19(lam, plane, off, fb, gfb, gsb);
   C pb = C(0), hv = C(0);
+  if (y == 0 || y == ny - 1) {
+    WallSource<C> w;
+    load_wall_source(SN, phi, x, y, nx, ny, pitch, plane, w);
+    fold_wall(P, w, fb, gfb, gsb, lam, wphib, plane, off, hv);
+  } else {
+    store19(lam, plane, off, fb, gfb, gsb);
+  }
   medium_adjoint<C>(P, ph, md, mdb, pb, hv);
   phib[off] += pb;
   hb[off] += hv;
 }
 
-// R1: fold the wall nodes' adjoints onto their interior neighbours.
-// Ring of interior nodes next to a wall: rows y = 1 and y = ny-2 (all
-// interior x), then columns x = 1 and x = nx-2 for 2 <= y <= ny-3.  Four
-// lanes of a warp serve one ring node: lane k folds the k-th wall node whose
-// rebuild reads it (at most three: a side wall, a bottom/top wall and a
-// corner, which the isothermal columns own), the lanes' contributions are
-// summed in a fixed butterfly order, and lane 0 adds the sum to the node's
-// adjoint -- so a corner costs one transposed rebuild of latency, not three.
-template <typename C>
-__device__ __forceinline__ C lane4_sum(C v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  return v;
-}
-
-template <typename C>
-__global__ void __launch_bounds__(128) k_adj_wall(C* __restrict__ lam,
-                                                  const C* __restrict__ Snext,
-                                                  const C* __restrict__ phi,
-                                                  C* __restrict__ phib, C* __restrict__ hb,
-                                                  const NodeParams<C> P, int nx, int ny,
-                                                  int64_t pitch, int64_t plane) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int q = t >> 2, lane = t & 3;
-  const int row = nx - 2, col = ny - 4;
-  // every lane reaches the shuffles; lanes past the ring only contribute zeros
-  const bool valid = q < 2 * row + 2 * col;
-  int x = 1, y = 1;
-  if (q < row) { x = 1 + q; y = 1; }
-  else if (q < 2 * row) { x = 1 + q - row; y = ny - 2; }
-  else if (q < 2 * row + col) { x = 1; y = 2 + q - 2 * row; }
-  else if (valid) { x = nx - 2; y = 2 + q - 2 * row - col; }
-  const int64_t off = (int64_t)y * pitch + x;
-  // wall nodes whose rebuild reads this node (isothermal columns own the corners)
-  int wx[3] = {0, 0, 0}, wy[3] = {0, 0, 0};
-  bool iso[3] = {false, false, false};
-  int nw = 0;
-  if (x == 1) { wx[nw] = 0; wy[nw] = y; iso[nw] = true; ++nw; }
-  if (x == nx - 2) { wx[nw] = nx - 1; wy[nw] = y; iso[nw] = true; ++nw; }
-  if (y == 1) { wx[nw] = x; wy[nw] = 0; iso[nw] = false; ++nw; }
-  if (y == ny - 2) { wx[nw] = x; wy[nw] = ny - 1; iso[nw] = false; ++nw; }
-  const bool cx0 = (x == 1), cx1 = (x == nx - 2), cy0 = (y == 1), cy1 = (y == ny - 2);
-  if (cx0 && cy0 && nw < 3) { wx[nw] = 0; wy[nw] = 0; iso[nw] = true; ++nw; }
-  if (cx0 && cy1 && nw < 3) { wx[nw] = 0; wy[nw] = ny - 1; iso[nw] = true; ++nw; }
-  if (cx1 && cy0 && nw < 3) { wx[nw] = nx - 1; wy[nw] = 0; iso[nw] = true; ++nw; }
-  if (cx1 && cy1 && nw < 3) { wx[nw] = nx - 1; wy[nw] = ny - 1; iso[nw] = true; ++nw; }
-  C cf[9] = {}, cgf[5] = {}, cgs[5] = {};
-  MediumBar<C> mdb;
-  zero(mdb);
-  const C ph = valid ? phi[off] : C(0.5);
-  const Medium<C> md = medium_at<C>(P, ph);
-  // lane 0 owns the ring node's adjoint: its load goes out first (no wall
-  // node store of this kernel touches it)
-  C L_f[9], L_gf[5], L_gs[5];
-  if (valid && lane == 0) load19(lam, plane, off, L_f, L_gf, L_gs);
-  if (valid && lane < nw) {
-    C f[9], gf[5], gs[5];
-    load19(Snext, plane, off, f, gf, gs);
-    const int64_t boff = (int64_t)wy[lane] * pitch + wx[lane];
-    C lf[9], lgf[5], lgs[5];
-    load19(lam, plane, boff, lf, lgf, lgs);
-    nee_adjoint<C>(P, md, f, gf, gs, iso[lane], lf, lgf, lgs, cf, cgf, cgs, mdb);
-    const C zf[9] = {}, zg[5] = {};
-    store19(lam, plane, boff, zf, zg, zg);  // a wall node's pulled values are unused
-  }
-#pragma unroll
-  for (int i = 0; i < 9; ++i) cf[i] = lane4_sum(cf[i]);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    cgf[i] = lane4_sum(cgf[i]);
-    cgs[i] = lane4_sum(cgs[i]);
-  }
-  mdb.phi = lane4_sum(mdb.phi);
-  mdb.inv_phi = lane4_sum(mdb.inv_phi);
-  mdb.a = lane4_sum(mdb.a);
-  mdb.b = lane4_sum(mdb.b);
-  mdb.inv_1d = lane4_sum(mdb.inv_1d);
-  mdb.c0 = lane4_sum(mdb.c0);
-  mdb.c1 = lane4_sum(mdb.c1);
-  mdb.l0 = lane4_sum(mdb.l0);
-  mdb.l1 = lane4_sum(mdb.l1);
-  if (!valid || lane != 0) return;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) L_f[i] += cf[i];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    L_gf[i] += cgf[i];
-    L_gs[i] += cgs[i];
-  }
-  store19(lam, plane, off, L_f, L_gf, L_gs);
-  C pb = C(0), hv = C(0);
-  medium_adjoint<C>(P, ph, md, mdb, pb, hv);
-  phib[off] += pb;
-  hb[off] += hv;
-}
-
-// R2: transposed streaming (gather from y + e_i) and transposed collision.
-template <typename C>
-__global__ void __launch_bounds__(256) k_adj_main(const C* __restrict__ Lam,
+// R2: transposed streaming (gather from y + e_i) and transposed collision;
+// a wall node's thread then folds its result (R1) unless S_n is the initial
+// state (fold = 0), whose wall nodes were not rebuilt.  The fold raises the
+// kernel's registers (119 against 73 without it, FP32).  Two builds of the
+// same code: kCapped = false keeps them all (lattices that fit one wave,
+// where the kernel's time is one thread's latency); kCapped = true caps them
+// so that four blocks share an SM (FP32; larger lattices, where occupancy
+// hides the latency), spilling a few values to local memory.
+template <typename C, bool kCapped>
+__global__ void __launch_bounds__(256, (kCapped && sizeof(C) == 4) ? 4 : 1)
+    k_adj_main(const C* __restrict__ Lam,
                                                   C* __restrict__ lam_out,
                                                   const C* __restrict__ S,
                                                   const C* __restrict__ phi,
                                                   C* __restrict__ phib, C* __restrict__ hb,
-                                                  const NodeParams<C> P, int nx, int ny,
-                                                  int64_t pitch, int64_t plane) {
+                                                  C* __restrict__ wphib, const NodeParams<C> P,
+                                                  int nx, int ny, int64_t pitch, int64_t plane,
+                                                  int fold) {
+  chain_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -253,6 +280,11 @@ __global__ void __launch_bounds__(256) k_adj_main(const C* __restrict__ Lam,
       qgs[i] = pulled ? Lam[(int64_t)(14 + i) * plane + toff] : C(0);
     }
   }
+  if (x <= 2 || x >= nx - 3 || y <= 2 || y >= ny - 3)
+    add_wall_folds(Lam, x, y, nx, ny, pitch, plane, qf, qgf, qgs);
+  const bool wall = fold && (x == 0 || x == nx - 1 || y == 0 || y == ny - 1);
+  WallSource<C> w;
+  if (wall) load_wall_source(S, phi, x, y, nx, ny, pitch, plane, w);
   C f[9], gf[5], gs[5];
   load19(S, plane, off, f, gf, gs);
   const C ph = phi[off];
@@ -261,11 +293,34 @@ __global__ void __launch_bounds__(256) k_adj_main(const C* __restrict__ Lam,
   MediumBar<C> mdb;
   zero(mdb);
   collide_adjoint<C>(P, md, f, gf, gs, qf, qgf, qgs, fb, gfb, gsb, mdb);
-  store19(lam_out, plane, off, fb, gfb, gsb);
   C pb = C(0), hv = C(0);
+  if (wall)
+    fold_wall(P, w, fb, gfb, gsb, lam_out, wphib, plane, off, hv);
+  else
+    store19(lam_out, plane, off, fb, gfb, gsb);
   medium_adjoint<C>(P, ph, md, mdb, pb, hv);
   phib[off] += pb;
   hb[off] += hv;
+}
+
+// The folds' porosity terms, kept in their wall nodes' places, added to the
+// interior node each wall node was rebuilt from (side column, bottom/top
+// row, corner: the order of the gather).
+template <typename C>
+__global__ void __launch_bounds__(256) k_add_wall_phib(C* __restrict__ phib,
+                                                       const C* __restrict__ wphib, int nx,
+                                                       int ny, int64_t pitch) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x < 1 || x > nx - 2 || y < 1 || y > ny - 2) return;
+  const bool cx = x == 1 || x == nx - 2, cy = y == 1 || y == ny - 2;
+  if (!cx && !cy) return;
+  const int wx = (x == 1) ? 0 : nx - 1, wy = (y == 1) ? 0 : ny - 1;
+  C acc = phib[(int64_t)y * pitch + x];
+  if (cx) acc += wphib[(int64_t)y * pitch + wx];
+  if (cy) acc += wphib[(int64_t)wy * pitch + x];
+  if (cx && cy) acc += wphib[(int64_t)wy * pitch + wx];
+  phib[(int64_t)y * pitch + x] = acc;
 }
 
 // FP64 sum of one plane (fixed grid and order: deterministic).
@@ -300,6 +355,7 @@ __global__ void k_sum_partials(const double* __restrict__ part, int n, double* _
 template <typename C>
 __global__ void __launch_bounds__(256) k_copy19(const C* __restrict__ src, C* __restrict__ dst,
                                                 int64_t n) {
+  chain_wait();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     dst[k] = src[k];
@@ -352,6 +408,24 @@ struct SegGraph {
   }
 };
 
+// Launch with programmatic stream serialisation when the previous operation
+// on the stream (or in the capture) is one of the kernels above.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(bool chained, void (*k)(KArgs...), dim3 grid, dim3 block,
+                           cudaStream_t s, Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 constexpr int kSumBlocks = 128;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -359,7 +433,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct AdjLayout {
   int64_t nseg = 0;
   size_t p19 = 0, pl = 0;  // bytes of 19 planes, of one plane
-  size_t ckpt = 0, slots = 0, seg0 = 0, pops = 0, lam = 0, phib = 0, hb = 0, part = 0, total = 0;
+  size_t ckpt = 0, slots = 0, seg0 = 0, pops = 0, lam = 0, phib = 0, hb = 0, wphib = 0, part = 0;
+  size_t total = 0;
 };
 
 AdjLayout adj_layout(const ltne_handle* h, int64_t n_steps, int32_t segment) {
@@ -383,6 +458,8 @@ AdjLayout adj_layout(const ltne_handle* h, int64_t n_steps, int32_t segment) {
   off += L.pl;
   L.hb = off;
   off += L.pl;
+  L.wphib = off;
+  off += L.pl;
   L.part = off;
   off += align_up((kSumBlocks + 1) * sizeof(double), A);
   L.total = off;
@@ -402,6 +479,7 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
   auto buf19 = [&](size_t base, int64_t k) { return reinterpret_cast<C*>(ws + base + k * L.p19); };
   C* phib = reinterpret_cast<C*>(ws + L.phib);
   C* hb = reinterpret_cast<C*>(ws + L.hb);
+  C* wphib = reinterpret_cast<C*>(ws + L.wphib);
   double* part = reinterpret_cast<double*>(ws + L.part);
   (void)pe;
 
@@ -421,12 +499,13 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
     e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return LTNE_ERR_CUDA;
   }
-  auto fwd_step = [&](cudaStream_t s_, int src_buf, int wm, C* rec) {
+  auto fwd_step = [&](cudaStream_t s_, int src_buf, int wm, C* rec, bool chained) {
     const C* src = reinterpret_cast<const C*>(h->ws + h->off_pop[src_buf]);
     C* dst = reinterpret_cast<C*>(h->ws + h->off_pop[src_buf ^ 1]);
-    k_step_record<C><<<grd, blk, 0, s_>>>(src, dst, phi, mac, P, nx, ny, pitch, plane, wm, rec);
-    return cudaGetLastError();
+    return launch_chained(chained, k_step_record<C>, grd, blk, s_, src, dst, phi, mac, P, nx, ny,
+                          pitch, plane, wm, rec);
   };
+  bool after_kernel = false;  // the stream's last operation is a kernel above
   SegGraph gf[2];
   int64_t n = 0;
   while (n < N && e == cudaSuccess) {
@@ -439,7 +518,7 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
           int b = par;
           cudaError_t le = cudaSuccess;
           for (int j = 0; j < K && le == cudaSuccess; ++j) {
-            le = fwd_step(cs, b, 0, j == 0 ? buf19(L.ckpt, 1) : nullptr);
+            le = fwd_step(cs, b, 0, j == 0 ? buf19(L.ckpt, 1) : nullptr, j > 0);
             b ^= 1;
           }
           return le;
@@ -456,12 +535,15 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
       C* imac = mac;
       void* args[] = {&src, &dst, &iphi, &imac, &iP, &inx, &iny, &ipitch, &iplane, &wm, &rec};
       e = gf[par].launch(reinterpret_cast<void*>(k_step_record<C>), grd, blk, args, st);
+      after_kernel = false;
       if (K & 1) h->cur ^= 1;
       h->step += K;
       h->launches += K;
       n += K;
     } else {
-      e = fwd_step(st, h->cur, n == N - 1 ? 1 : 0, records ? buf19(L.ckpt, a / K) : nullptr);
+      e = fwd_step(st, h->cur, n == N - 1 ? 1 : 0, records ? buf19(L.ckpt, a / K) : nullptr,
+                   after_kernel);
+      after_kernel = true;
       h->cur ^= 1;
       ++h->step;
       ++h->launches;
@@ -483,57 +565,80 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
 
   // ---- reverse
   e = cudaMemsetAsync(ws + L.lam, 0, 2 * L.p19, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.phib, 0, 2 * L.pl, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.phib, 0, 3 * L.pl, st);  // phib, hb, wphib
   if (e != cudaSuccess) return LTNE_ERR_CUDA;
+  after_kernel = false;
   C* lamL = buf19(L.lam, 0);
   C* lamO = buf19(L.lam, 1);
   const C inv_dT = C(1.0 / (h->p.T_hot - h->p.T_cold));
-  const int ring = 2 * (nx - 2) + 2 * (ny - 4);
   const int64_t n19 = 19 * plane;
+  bool capped = h->adj_sched == LTNE_ADJ_CAPPED;
+  if (h->adj_sched == LTNE_ADJ_AUTO) {
+    // all registers when the transposed-collision grid fits one wave
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_main<C, false>,
+                                                        (int)(blk.x * blk.y), 0);
+    if (e != cudaSuccess) return LTNE_ERR_CUDA;
+    capped = (int64_t)grd.x * grd.y > (int64_t)sms * per_sm;
+  }
   // One segment's recompute and reverse sweep; slot 0 is S_a.
-  auto segment_body = [&](cudaStream_t s_, int64_t len, C* slot0, bool seed, C*& lL, C*& lO) {
+  // The first kernel is chained when the stream's previous operation is one
+  // of these kernels; the rest always are.  The segment that starts at step
+  // 0 does not fold its last adjoint (the initial state's wall nodes).
+  auto segment_body = [&](cudaStream_t s_, int64_t len, C* slot0, bool seed, C*& lL, C*& lO,
+                          bool chained, bool initial) {
     auto slot = [&](int64_t j) { return j == 0 ? slot0 : buf19(L.slots, j - 1); };
     C* p0 = buf19(L.pops, 0);
     C* p1 = buf19(L.pops, 1);
-    k_collide_pre<C><<<grd, blk, 0, s_>>>(slot(0), p0, phi, P, nx, ny, pitch, plane);
-    for (int64_t j = 1; j <= len; ++j) {
-      k_step_record<C><<<grd, blk, 0, s_>>>(p0, p1, phi, mac, P, nx, ny, pitch, plane, 0,
-                                            slot(j));
+    cudaError_t le = launch_chained(chained, k_collide_pre<C>, grd, blk, s_, (const C*)slot(0),
+                                    p0, phi, P, nx, ny, pitch, plane);
+    for (int64_t j = 1; j <= len && le == cudaSuccess; ++j) {
+      le = launch_chained(true, k_step_record<C>, grd, blk, s_, (const C*)p0, p1, phi, mac, P,
+                          nx, ny, pitch, plane, 0, slot(j));
       C* t = p0;
       p0 = p1;
       p1 = t;
     }
-    if (seed)
-      k_adj_seed<C><<<(2 * ny + 255) / 256, 256, 0, s_>>>(slot(len), lL, phi, phib, hb, P, nx,
-                                                          ny, pitch, plane, inv_dT);
-    for (int64_t j = len - 1; j >= 0; --j) {
-      if (ring > 0)
-        k_adj_wall<C><<<(4 * ring + 127) / 128, 128, 0, s_>>>(lL, slot(j + 1), phi, phib, hb, P,
-                                                              nx, ny, pitch, plane);
-      k_adj_main<C><<<grd, blk, 0, s_>>>(lL, lO, slot(j), phi, phib, hb, P, nx, ny, pitch,
-                                         plane);
+    if (seed && le == cudaSuccess)
+      le = launch_chained(true, k_adj_seed<C>, dim3((2 * ny + 255) / 256), dim3(256), s_,
+                          (const C*)slot(len), lL, phi, phib, hb, wphib, P, nx, ny, pitch, plane,
+                          inv_dT);
+    for (int64_t j = len - 1; j >= 0 && le == cudaSuccess; --j) {
+      const int fold = (initial && j == 0) ? 0 : 1;
+      if (capped)
+        le = launch_chained(true, k_adj_main<C, true>, grd, blk, s_, (const C*)lL, lO,
+                            (const C*)slot(j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
+                            fold);
+      else
+        le = launch_chained(true, k_adj_main<C, false>, grd, blk, s_, (const C*)lL, lO,
+                            (const C*)slot(j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
+                            fold);
       C* t = lL;
       lL = lO;
       lO = t;
     }
-    return cudaGetLastError();
+    return le;
   };
-  // Full segments other than the last replay one graph (per adjoint-buffer
-  // parity) whose root copies the segment's checkpoint into slot 0.
+  // Full segments other than the last and the first replay one graph (per
+  // adjoint-buffer parity) whose root copies the segment's checkpoint into
+  // slot 0.
   SegGraph gr[2];
   C* seg0 = buf19(L.seg0, 0);
   const dim3 cgrid(1216), cblk(256);
   for (int64_t s = L.nseg - 1; s >= 0 && e == cudaSuccess; --s) {
     const int64_t a = s * K, b = (a + K < N) ? a + K : N;
     const bool last = (s == L.nseg - 1);
-    if (!last && b - a == K && K > 1) {
+    if (!last && s > 0 && b - a == K && K > 1) {
       const int par = (lamL == buf19(L.lam, 0)) ? 0 : 1;
       if (!gr[par].exec)
         e = gr[par].capture(h->cap_stream, [&](cudaStream_t cs) {
           k_copy19<C><<<cgrid, cblk, 0, cs>>>(buf19(L.ckpt, 0), seg0, n19);
           C* lL = buf19(L.lam, par);
           C* lO = buf19(L.lam, par ^ 1);
-          return segment_body(cs, K, seg0, false, lL, lO);
+          return segment_body(cs, K, seg0, false, lL, lO, true, false);
         });
       if (e != cudaSuccess) break;
       const C* src = buf19(L.ckpt, s);
@@ -541,17 +646,20 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
       int64_t cnt = n19;
       void* args[] = {&src, &dst, &cnt};
       e = gr[par].launch(reinterpret_cast<void*>(k_copy19<C>), cgrid, cblk, args, st);
+      after_kernel = false;
       if (K & 1) {
         C* t = lamL;
         lamL = lamO;
         lamO = t;
       }
     } else {
-      e = segment_body(st, b - a, buf19(L.ckpt, s), last, lamL, lamO);
+      e = segment_body(st, b - a, buf19(L.ckpt, s), last, lamL, lamO, after_kernel, s == 0);
+      after_kernel = true;
     }
   }
   if (e != cudaSuccess) return LTNE_ERR_CUDA;
   // ---- outputs
+  k_add_wall_phib<C><<<grd, blk, 0, st>>>(phib, wphib, nx, ny, pitch);
   k_sum_plane<C><<<kSumBlocks, kRB, 0, st>>>(hb, nx, ny, pitch, part);
   k_sum_partials<<<1, 32, 0, st>>>(part, kSumBlocks, part + kSumBlocks);
   e = cudaGetLastError();
@@ -571,6 +679,18 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
 }  // namespace
 
 extern "C" {
+
+int ltne_set_adjoint_schedule(ltne_handle* h, int32_t mode) {
+  if (!h || mode < LTNE_ADJ_AUTO || mode > LTNE_ADJ_CAPPED) return LTNE_ERR_INVALID_ARG;
+  h->adj_sched = mode;
+  return LTNE_OK;
+}
+
+int ltne_get_adjoint_schedule(const ltne_handle* h, int32_t* mode) {
+  if (!h || !mode) return LTNE_ERR_INVALID_ARG;
+  *mode = h->adj_sched;
+  return LTNE_OK;
+}
 
 size_t ltne_adjoint_workspace_bytes(const ltne_handle* h, int64_t n_steps, int32_t segment) {
   if (!h || n_steps < 1 || segment < 1) return 0;

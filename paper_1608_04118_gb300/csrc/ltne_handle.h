@@ -31,6 +31,7 @@ struct ltne_handle {
   float enc_scale = 1.0f;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t launches = 0;
+  int32_t adj_sched = 0;  // LTNE_ADJ_*
   // two pinned host buffers that stage whole fields in and out (allocated
   // at the first set_fields / get_fields, freed by ltne_destroy)
   char* pin[2] = {nullptr, nullptr};

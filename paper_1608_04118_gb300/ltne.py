@@ -27,6 +27,7 @@ LTNE_ERR_WORKSPACE = 7
 
 LTNE_F64, LTNE_F32, LTNE_F16DEV, LTNE_BF16DEV = 0, 1, 2, 3
 LTNE_BC_CAVITY, LTNE_BC_PERIODIC, LTNE_BC_CHANNEL = 0, 1, 2
+LTNE_ADJ_AUTO, LTNE_ADJ_ONE_WAVE, LTNE_ADJ_CAPPED = 0, 1, 2
 LTNE_K_DARCY, LTNE_K_ERGUN = 0, 1
 
 STORAGE = {"f64": LTNE_F64, "f32": LTNE_F32, "f16": LTNE_F16DEV, "bf16": LTNE_BF16DEV}
@@ -98,6 +99,8 @@ SIGNATURES = {
     "ltne_get_staging": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "ltne_observables_static": (C.c_int, [C.POINTER(ltne_params), _vp, C.c_int64, _vp, C.c_int64,
                                           _vp, C.POINTER(ltne_obs)]),
+    "ltne_set_adjoint_schedule": (C.c_int, [_vp, C.c_int32]),
+    "ltne_get_adjoint_schedule": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "ltne_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_int64, C.c_int32]),
     "ltne_adjoint": (C.c_int, [_vp, _dp, _dp, _dp, _dp, C.c_int64, C.c_int32, _vp, C.c_size_t, _vp,
                                _dp, _dp]),
@@ -256,6 +259,16 @@ def ltne_check_bounded_wait(stream_ptr, spins) -> int:
     return v.value
 
 
+def ltne_set_adjoint_schedule(h, mode):
+    _check(_lib().ltne_set_adjoint_schedule(h, int(mode)), "ltne_set_adjoint_schedule")
+
+
+def ltne_get_adjoint_schedule(h) -> int:
+    v = C.c_int32()
+    _check(_lib().ltne_get_adjoint_schedule(h, C.byref(v)), "ltne_get_adjoint_schedule")
+    return v.value
+
+
 def ltne_get_staging(h) -> int:
     v = C.c_int32()
     _check(_lib().ltne_get_staging(h, C.byref(v)), "ltne_get_staging")
@@ -385,6 +398,16 @@ class Cavity:
     @property
     def staging(self):
         return ltne_get_staging(self.h)
+
+    def set_adjoint_schedule(self, mode):
+        """Register budget of the adjoint's transposed collision: 0 by lattice
+        size, 1 all registers (one wave), 2 capped (four blocks per SM)."""
+        ltne_set_adjoint_schedule(self.h, mode)
+        return self
+
+    @property
+    def adjoint_schedule(self):
+        return ltne_get_adjoint_schedule(self.h)
 
     def adjoint(self, porosity, n_steps, segment=None, rho=None, T_f=None, T_s=None):
         """Run n_steps from the given initial fields (fluid at rest) and return

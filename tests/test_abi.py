@@ -160,6 +160,13 @@ def test_option_validation_without_gpu(lt):
                             C.byref(J), C.byref(dH)) == lt.LTNE_ERR_STATE
     assert lt.ltne_adjoint_workspace_bytes(h, 100, 10) > 0
     assert lt.ltne_adjoint_workspace_bytes(h, 0, 10) == 0
+    # adjoint register budget: by size by default, either build on request
+    assert lt.ltne_get_adjoint_schedule(h) == lt.LTNE_ADJ_AUTO
+    for bad in (-1, 3):
+        assert lib.ltne_set_adjoint_schedule(h, bad) == lt.LTNE_ERR_INVALID_ARG
+    for mode in (lt.LTNE_ADJ_CAPPED, lt.LTNE_ADJ_ONE_WAVE, lt.LTNE_ADJ_AUTO):
+        assert lib.ltne_set_adjoint_schedule(h, mode) == lt.LTNE_OK
+        assert lt.ltne_get_adjoint_schedule(h) == mode
     lt.ltne_destroy(h)
     # step schedules: default per storage type; two nodes per thread need
     # float arithmetic and at most 128 threads per block

@@ -71,6 +71,53 @@ def test_adjoint_matches_complex_step_oracle(small_reference, storage, tol):
     assert 0.5 * (ob["Nu_f_hot"] + ob["Nu_s_hot"]) == pytest.approx(J, rel=1e-12)
 
 
+@pytest.mark.parametrize("sched", [1, 2])
+@pytest.mark.parametrize("nx,ny,seg", [(4, 4, 3), (6, 5, 7), (9, 7, 40)])
+def test_every_node_on_tiny_cavities(nx, ny, seg, sched):
+    """The gradient at every node -- walls, corners and the interior nodes the
+    walls are rebuilt from included -- against the complex-step oracle, FP64,
+    40 steps: in segments of 3 (graph replays between a first and a last
+    segment run on the stream), of 7 (ragged) and in one segment; both
+    register budgets of the transposed collision."""
+    cfg = dict(SMALL, nx=nx, ny=ny, Ra=1e3, Da=1e-2)
+    phi = W.porosity_field(nx, ny, 0.4, 0.8, seed=50 + nx).reshape(-1)
+    ref = _complex_step(cfg, phi, 40, range(nx * ny))
+    cav = cavity_for(cfg, storage="f64", phi=phi).set_adjoint_schedule(sched)
+    J, g, dH = cav.adjoint(phi, 40, segment=seg)
+    g = g.cpu().numpy().reshape(-1)
+    gref = np.array([ref[k] for k in range(nx * ny)])
+    assert J == pytest.approx(ref["J"], rel=1e-12)
+    assert np.abs(g - gref).max() <= 1e-9 * np.abs(gref).max(), np.abs(g - gref).reshape(ny, nx)
+    assert dH == pytest.approx(ref[-1], rel=1e-9)
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f64", 1e-12)])
+def test_register_budgets_agree(storage, tol):
+    """Both builds of the transposed collision, and the size-based choice, on
+    a lattice that fits one wave (all registers by default) and on one that
+    does not (capped by default): the default gives the bits of the build it
+    picks, a repeated run the same bits, and the other build agrees to
+    rounding (under a register cap the compiler may contract a different
+    set of multiply-adds)."""
+    for nx, ny, auto in ((40, 30, 1), (400, 300, 2)):
+        cfg = dict(SMALL, nx=nx, ny=ny)
+        phi = W.porosity_field(nx, ny, 0.4, 0.8, seed=60).reshape(-1)
+        outs = {}
+        for sched in (0, 1, 2, 1):
+            cav = cavity_for(cfg, storage=storage, phi=phi).set_adjoint_schedule(sched)
+            J, g, dH = cav.adjoint(phi, 30, segment=6)
+            outs.setdefault(sched, []).append((J, g.double().cpu().numpy(), dH))
+            cav.close()
+        a, b = outs[0][0], outs[auto][0]
+        assert a[0] == b[0] and a[2] == b[2] and np.array_equal(a[1], b[1])
+        r1, r2 = outs[1]
+        assert r1[0] == r2[0] and r1[2] == r2[2] and np.array_equal(r1[1], r2[1])
+        c = outs[2][0]
+        assert c[0] == r1[0]  # J: the forward pass is the same
+        assert c[2] == pytest.approx(r1[2], rel=tol)
+        assert np.abs(c[1] - r1[1]).max() <= tol * np.abs(r1[1]).max()
+
+
 def test_segment_length_does_not_change_the_gradient(small_reference):
     phi, nodes, _ = small_reference
     outs = []
