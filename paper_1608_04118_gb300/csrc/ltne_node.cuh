@@ -442,16 +442,18 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   return h;
 }
 
-// Marsaglia's xorshift32 stream seeded from fmix32(node ^ fmix32(step)).
+// A 32-bit linear congruential stream (Numerical Recipes' multiplier and
+// increment) seeded from fmix32(node ^ fmix32(step)); each word is the state
+// with its upper half folded onto the lower (x ^ (x >> 16)), so that the low
+// bits, whose periods are short in the raw state, mix in the upper ones.
+// Three instructions per word; the seed hash decorrelates nodes and steps.
 struct RandomBits {
   uint32_t s;
   __device__ __forceinline__ RandomBits(uint32_t node, uint32_t step)
-      : s(fmix32(node ^ fmix32(step * 0x9e3779b9u + 0x7f4a7c15u)) | 1u) {}
+      : s(fmix32(node ^ fmix32(step * 0x9e3779b9u + 0x7f4a7c15u))) {}
   __device__ __forceinline__ uint32_t next() {
-    s ^= s << 13;
-    s ^= s >> 17;
-    s ^= s << 5;
-    return s;
+    s = s * 1664525u + 1013904223u;
+    return s ^ (s >> 16);
   }
 };
 
