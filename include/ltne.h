@@ -268,7 +268,9 @@ int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
 /* Bytes of the adjoint workspace (caller-owned device memory): checkpoints
    of the pre-collision state at every segment start, `segment` recompute
    slots, adjoint and gradient buffers; about
-   (ceil(n_steps/segment) + segment + 4) * 19 planes of the compute type. */
+   (ceil(n_steps/segment) + 2 segment + 6) * 19 planes of the compute type
+   (two sets of recompute slots: one segment is reversed while the one
+   before it is recomputed). */
 size_t ltne_adjoint_workspace_bytes(const ltne_handle* h, int64_t n_steps, int32_t segment);
 
 /* Register budget of the adjoint's transposed-collision kernel (no

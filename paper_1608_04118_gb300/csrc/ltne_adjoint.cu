@@ -26,7 +26,8 @@
 // Memory: sqrt(T)-style checkpointing.  The forward pass records S_a at the
 // start of every segment of K steps; the reverse sweep recomputes each
 // segment's S_{a+1..a+K} from its checkpoint into K slots, then walks back
-// through it.  Total extra work: one forward pass.
+// through it.  Total extra work: one forward pass, run on a second stream
+// beside the reverse sweep of the segment after it.
 #include <math.h>
 #include <string.h>
 
@@ -426,6 +427,20 @@ cudaError_t launch_chained(bool chained, void (*k)(KArgs...), dim3 grid, dim3 bl
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+// Two events for a fork and a join between streams (no timing).
+struct EventPair {
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    return e;
+  }
+  ~EventPair() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+  }
+};
+
 constexpr int kSumBlocks = 128;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -446,10 +461,10 @@ AdjLayout adj_layout(const ltne_handle* h, int64_t n_steps, int32_t segment) {
   size_t off = 0;
   L.ckpt = off;
   off += (size_t)L.nseg * L.p19;
-  L.slots = off;
-  off += (size_t)segment * L.p19;
-  L.seg0 = off;  // copy of the segment's checkpoint for graph replay
-  off += L.p19;
+  L.slots = off;  // two sets: one being reversed, one being recomputed
+  off += 2 * (size_t)segment * L.p19;
+  L.seg0 = off;  // the segments' checkpoints copied for graph replay (two)
+  off += 2 * L.p19;
   L.pops = off;
   off += 2 * L.p19;
   L.lam = off;
@@ -584,78 +599,144 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
     if (e != cudaSuccess) return LTNE_ERR_CUDA;
     capped = (int64_t)grd.x * grd.y > (int64_t)sms * per_sm;
   }
-  // One segment's recompute and reverse sweep; slot 0 is S_a.
-  // The first kernel is chained when the stream's previous operation is one
-  // of these kernels; the rest always are.  The segment that starts at step
-  // 0 does not fold its last adjoint (the initial state's wall nodes).
-  auto segment_body = [&](cudaStream_t s_, int64_t len, C* slot0, bool seed, C*& lL, C*& lO,
-                          bool chained, bool initial) {
-    auto slot = [&](int64_t j) { return j == 0 ? slot0 : buf19(L.slots, j - 1); };
+  // Slot set q holds a segment's states: slot 0 (S_a, copied from its
+  // checkpoint) and K recomputed slots.  The sweep reverses segment s from
+  // one set while segment s - 1 is recomputed into the other on a second
+  // stream: at small lattices every kernel is a single wave bound by one
+  // thread's latency, and the two chains share the SMs.
+  const dim3 cgrid(1216), cblk(256);
+  auto slot = [&](int q, int64_t j) {
+    return j == 0 ? buf19(L.seg0, q) : buf19(L.slots, (int64_t)q * K + j - 1);
+  };
+  // Copy of the checkpoint into slot 0 (a graph's root), then the recompute.
+  auto recompute_body = [&](cudaStream_t s_, int64_t len, const C* ckpt, int q, bool chained) {
+    cudaError_t le = launch_chained(chained, k_copy19<C>, cgrid, cblk, s_, ckpt, slot(q, 0), n19);
     C* p0 = buf19(L.pops, 0);
     C* p1 = buf19(L.pops, 1);
-    cudaError_t le = launch_chained(chained, k_collide_pre<C>, grd, blk, s_, (const C*)slot(0),
-                                    p0, phi, P, nx, ny, pitch, plane);
+    if (le == cudaSuccess)
+      le = launch_chained(true, k_collide_pre<C>, grd, blk, s_, (const C*)slot(q, 0), p0, phi, P,
+                          nx, ny, pitch, plane);
     for (int64_t j = 1; j <= len && le == cudaSuccess; ++j) {
       le = launch_chained(true, k_step_record<C>, grd, blk, s_, (const C*)p0, p1, phi, mac, P,
-                          nx, ny, pitch, plane, 0, slot(j));
+                          nx, ny, pitch, plane, 0, slot(q, j));
       C* t = p0;
       p0 = p1;
       p1 = t;
     }
-    if (seed && le == cudaSuccess)
-      le = launch_chained(true, k_adj_seed<C>, dim3((2 * ny + 255) / 256), dim3(256), s_,
-                          (const C*)slot(len), lL, phi, phib, hb, wphib, P, nx, ny, pitch, plane,
-                          inv_dT);
+    return le;
+  };
+  // The reverse sweep over set q (the seed first on the last segment); the
+  // segment that starts at step 0 does not fold its last adjoint (the
+  // initial state's wall nodes were not rebuilt).
+  auto reverse_body = [&](cudaStream_t s_, int64_t len, int q, bool seed, C*& lL, C*& lO,
+                          bool chained, bool initial) {
+    cudaError_t le = cudaSuccess;
+    if (seed) {
+      le = launch_chained(chained, k_adj_seed<C>, dim3((2 * ny + 255) / 256), dim3(256), s_,
+                          (const C*)slot(q, len), lL, phi, phib, hb, wphib, P, nx, ny, pitch,
+                          plane, inv_dT);
+      chained = true;
+    }
     for (int64_t j = len - 1; j >= 0 && le == cudaSuccess; --j) {
       const int fold = (initial && j == 0) ? 0 : 1;
       if (capped)
-        le = launch_chained(true, k_adj_main<C, true>, grd, blk, s_, (const C*)lL, lO,
-                            (const C*)slot(j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
+        le = launch_chained(chained, k_adj_main<C, true>, grd, blk, s_, (const C*)lL, lO,
+                            (const C*)slot(q, j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
                             fold);
       else
-        le = launch_chained(true, k_adj_main<C, false>, grd, blk, s_, (const C*)lL, lO,
-                            (const C*)slot(j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
+        le = launch_chained(chained, k_adj_main<C, false>, grd, blk, s_, (const C*)lL, lO,
+                            (const C*)slot(q, j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
                             fold);
+      chained = true;
       C* t = lL;
       lL = lO;
       lO = t;
     }
     return le;
   };
-  // Full segments other than the last and the first replay one graph (per
-  // adjoint-buffer parity) whose root copies the segment's checkpoint into
-  // slot 0.
-  SegGraph gr[2];
-  C* seg0 = buf19(L.seg0, 0);
-  const dim3 cgrid(1216), cblk(256);
-  for (int64_t s = L.nseg - 1; s >= 0 && e == cudaSuccess; --s) {
-    const int64_t a = s * K, b = (a + K < N) ? a + K : N;
-    const bool last = (s == L.nseg - 1);
-    if (!last && s > 0 && b - a == K && K > 1) {
-      const int par = (lamL == buf19(L.lam, 0)) ? 0 : 1;
-      if (!gr[par].exec)
-        e = gr[par].capture(h->cap_stream, [&](cudaStream_t cs) {
-          k_copy19<C><<<cgrid, cblk, 0, cs>>>(buf19(L.ckpt, 0), seg0, n19);
-          C* lL = buf19(L.lam, par);
-          C* lO = buf19(L.lam, par ^ 1);
-          return segment_body(cs, K, seg0, false, lL, lO, true, false);
+  if (!h->aux_stream) {
+    e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return LTNE_ERR_CUDA;
+  }
+  EventPair ev;
+  if (ev.create() != cudaSuccess) return LTNE_ERR_CUDA;
+  const cudaStream_t st2 = h->aux_stream;
+  // Reverse of segment s on `main_s` while segment s - 1 (if any) is
+  // recomputed on `aux`, joined at the end.
+  auto iteration = [&](cudaStream_t main_s, cudaStream_t aux, int64_t s, int q, C*& lL, C*& lO,
+                       bool chained) {
+    const int64_t a = s * K, len = ((a + K < N) ? a + K : N) - a;
+    cudaError_t le = cudaSuccess;
+    if (s > 0) {
+      le = cudaEventRecord(ev.fork, main_s);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(aux, ev.fork, 0);
+      if (le == cudaSuccess) le = recompute_body(aux, K, buf19(L.ckpt, s - 1), q ^ 1, false);
+      chained = false;
+    }
+    if (le == cudaSuccess)
+      le = reverse_body(main_s, len, q, s == L.nseg - 1, lL, lO, chained, s == 0);
+    if (s > 0 && le == cudaSuccess) {
+      le = cudaEventRecord(ev.join, aux);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(main_s, ev.join, 0);
+    }
+    return le;
+  };
+  // Full segments other than the last and the first replay one captured
+  // iteration per (slot set, adjoint-buffer parity); its root copies
+  // segment s - 1's checkpoint into slot 0 of the other set, the only
+  // argument that changes between replays.
+  SegGraph gr[2][2];
+  int q = 0;
+  const int64_t last = L.nseg - 1;
+  e = recompute_body(st, N - last * K, buf19(L.ckpt, last), q, after_kernel);
+  after_kernel = true;
+  for (int64_t s = last; s >= 0 && e == cudaSuccess; --s) {
+    if (s != last && s > 0 && K > 1) {
+      const int lp = (lamL == buf19(L.lam, 0)) ? 0 : 1;
+      SegGraph& g = gr[q][lp];
+      if (!g.exec)
+        e = g.capture(h->cap_stream, [&](cudaStream_t cs) {
+          C* seg_next = slot(q ^ 1, 0);
+          k_copy19<C><<<cgrid, cblk, 0, cs>>>(buf19(L.ckpt, 0), seg_next, n19);
+          cudaError_t le = cudaGetLastError();
+          if (le == cudaSuccess) le = cudaEventRecord(ev.fork, cs);
+          if (le == cudaSuccess) le = cudaStreamWaitEvent(st2, ev.fork, 0);
+          // the recompute without its copy (the root)
+          C* p0 = buf19(L.pops, 0);
+          C* p1 = buf19(L.pops, 1);
+          if (le == cudaSuccess)
+            le = launch_chained(false, k_collide_pre<C>, grd, blk, st2, (const C*)seg_next, p0,
+                                phi, P, nx, ny, pitch, plane);
+          for (int64_t j = 1; j <= K && le == cudaSuccess; ++j) {
+            le = launch_chained(true, k_step_record<C>, grd, blk, st2, (const C*)p0, p1, phi,
+                                mac, P, nx, ny, pitch, plane, 0, slot(q ^ 1, j));
+            C* t = p0;
+            p0 = p1;
+            p1 = t;
+          }
+          C* lL = buf19(L.lam, lp);
+          C* lO = buf19(L.lam, lp ^ 1);
+          if (le == cudaSuccess) le = reverse_body(cs, K, q, false, lL, lO, false, false);
+          if (le == cudaSuccess) le = cudaEventRecord(ev.join, st2);
+          if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, ev.join, 0);
+          return le;
         });
       if (e != cudaSuccess) break;
-      const C* src = buf19(L.ckpt, s);
-      C* dst = seg0;
+      const C* src = buf19(L.ckpt, s - 1);
+      C* dst = slot(q ^ 1, 0);
       int64_t cnt = n19;
       void* args[] = {&src, &dst, &cnt};
-      e = gr[par].launch(reinterpret_cast<void*>(k_copy19<C>), cgrid, cblk, args, st);
-      after_kernel = false;
+      e = g.launch(reinterpret_cast<void*>(k_copy19<C>), cgrid, cblk, args, st);
       if (K & 1) {
         C* t = lamL;
         lamL = lamO;
         lamO = t;
       }
     } else {
-      e = segment_body(st, b - a, buf19(L.ckpt, s), last, lamL, lamO, after_kernel, s == 0);
-      after_kernel = true;
+      e = iteration(st, st2, s, q, lamL, lamO, after_kernel);
     }
+    after_kernel = false;
+    q ^= 1;
   }
   if (e != cudaSuccess) return LTNE_ERR_CUDA;
   // ---- outputs

@@ -1030,6 +1030,7 @@ void ltne_destroy(ltne_handle* h) {
   drop_graphs(h);
   release_pinned(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   delete h;
 }
 

@@ -10,6 +10,7 @@ struct ltne_handle {
   ltne_params p;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;  // the adjoint's recompute
   ltne::NodeParams<double> P{};
   ltne::StepShape shape;
   // derived lattice values
