@@ -260,12 +260,20 @@ __global__ void __launch_bounds__(256, (kCapped && sizeof(C) == 4) ? 4 : 1)
                                                   C* __restrict__ phib, C* __restrict__ hb,
                                                   C* __restrict__ wphib, const NodeParams<C> P,
                                                   int nx, int ny, int64_t pitch, int64_t plane,
-                                                  int fold) {
+                                                  int fold, const C* __restrict__ S_prev) {
   chain_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int64_t off = (int64_t)y * pitch + x;
+  // the next reverse step's state, recomputed a whole segment ago and mostly
+  // evicted to HBM by now: fetched into L2 while this step runs (one-wave
+  // build only: on larger lattices, bound by HBM throughput, it cost 4 %)
+  if (!kCapped && S_prev && (x & 7) == 0) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(S_prev + (int64_t)i * plane + off));
+  }
   // e_i of Eq. 8
   const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -639,14 +647,15 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
     }
     for (int64_t j = len - 1; j >= 0 && le == cudaSuccess; --j) {
       const int fold = (initial && j == 0) ? 0 : 1;
+      const C* pre = j > 0 ? slot(q, j - 1) : nullptr;
       if (capped)
         le = launch_chained(chained, k_adj_main<C, true>, grd, blk, s_, (const C*)lL, lO,
                             (const C*)slot(q, j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
-                            fold);
+                            fold, pre);
       else
         le = launch_chained(chained, k_adj_main<C, false>, grd, blk, s_, (const C*)lL, lO,
                             (const C*)slot(q, j), phi, phib, hb, wphib, P, nx, ny, pitch, plane,
-                            fold);
+                            fold, pre);
       chained = true;
       C* t = lL;
       lL = lO;
