@@ -202,18 +202,37 @@ def cpu_baseline_oracle(n, target_s=12.0):
     p = OracleParams.make(m, m, ergun_K=1, Ra=c["Ra"], Pr=c["Pr"], Da=c["Da"], H=c["H"],
                           gamma_sf=c["gamma_sf"], sigma=c["sigma"], T_hot=c["T_hot"],
                           T_cold=c["T_cold"], T_ref=c["T_ref"])
-    o = Oracle(p, phi=phi).init()
+    def timed(o, secs):
+        t0 = time.perf_counter()
+        o.step(1)
+        one = time.perf_counter() - t0
+        k = max(1, int(secs / max(one, 1e-6)))
+        t0 = time.perf_counter()
+        o.step(k)
+        return k, time.perf_counter() - t0
+
+    cores = oracle.num_threads()
+    k, dt = timed(Oracle(p, phi=phi).init(), target_s)
+    # the same sample on one core, and the 64 x 64 FP64 configuration's
+    # 10^4 steps on all cores
+    oracle.set_num_threads(1)
+    k1, dt1 = timed(Oracle(p, phi=phi).init(), target_s / 2)
+    oracle.set_num_threads(cores)
+    c1 = W.C1_PLAIN_64
+    p1 = OracleParams.make(c1["nx"], c1["ny"], ergun_K=0,
+                           **{q: c1[q] for q in ("Ra", "Pr", "Da", "porosity", "H", "gamma_sf",
+                                                 "sigma", "T_hot", "T_cold", "T_ref")})
+    o1 = Oracle(p1).init()
     t0 = time.perf_counter()
-    o.step(1)
-    one = time.perf_counter() - t0
-    k = max(1, int(target_s / max(one, 1e-6)))
-    t0 = time.perf_counter()
-    o.step(k)
-    dt = time.perf_counter() - t0
-    return {"value": m * m * k / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+    o1.step(c1["steps"])
+    dt_c1 = time.perf_counter() - t0
+    return {"value": m * m * k / dt / 1e6, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "FP64 oracle, %dx%d cavity with the same physics, %d steps (%.1f s)"
-                      % (m, m, k, dt)}
+                      % (m, m, k, dt),
+            "one_core": {"value": m * m * k1 / dt1 / 1e6, "unit": UNIT,
+                         "sample": "%d steps (%.1f s)" % (k1, dt1)},
+            "c1_64x64_1e4_steps_s": dt_c1}
 
 
 def run_reference(args):

@@ -12,4 +12,5 @@ from .ltne_oracle import (  # noqa: F401
     ergun_diameter,
     lattice_tables,
     num_threads,
+    set_num_threads,
 )

@@ -113,6 +113,7 @@ def _load():
         lib.orc_node.argtypes = [C.c_void_p, C.c_int] + [dp] * 9
         lib.orc_equilibria.argtypes = [C.c_void_p] + [C.c_double] * 8 + [dp] * 5
         lib.orc_num_threads.restype = C.c_int
+        lib.orc_set_num_threads.argtypes = [C.c_int]
         lib.orc_ergun_diameter.restype = C.c_double
         lib.orc_ergun_diameter.argtypes = [dp, C.c_long, C.c_double, C.c_double]
         _lib = lib
@@ -136,6 +137,11 @@ def _f64(a, n=None):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's node loops from now on (timing only)."""
+    _load().orc_set_num_threads(int(n))
 
 
 def ergun_diameter(phi, L, Da) -> float:
