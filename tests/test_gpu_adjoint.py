@@ -91,6 +91,28 @@ def test_every_node_on_tiny_cavities(nx, ny, seg, sched):
     assert dH == pytest.approx(ref[-1], rel=1e-9)
 
 
+@pytest.mark.parametrize("steps,seg", [(1, 1), (1, 4), (2, 1), (3, 2), (5, 2)])
+def test_fewest_steps(steps, seg):
+    """One to five steps in segments of one or two (a last segment of one
+    step, a single ragged segment, a segment longer than the run): every
+    node against the complex-step oracle, FP64.  After one or two steps the
+    wall Nusselt numbers do not yet depend on the porosity (the fluid starts
+    at rest and both phases at one temperature): the gradient is zero up to
+    round-off on both sides."""
+    nx, ny = 6, 5
+    cfg = dict(SMALL, nx=nx, ny=ny, Ra=1e3, Da=1e-2)
+    phi = W.porosity_field(nx, ny, 0.4, 0.8, seed=80 + steps).reshape(-1)
+    ref = _complex_step(cfg, phi, steps, range(nx * ny))
+    cav = cavity_for(cfg, storage="f64", phi=phi)
+    J, g, dH = cav.adjoint(phi, steps, segment=seg)
+    g = g.cpu().numpy().reshape(-1)
+    gref = np.array([ref[k] for k in range(nx * ny)])
+    assert J == pytest.approx(ref["J"], rel=1e-12)
+    assert np.abs(g - gref).max() <= 1e-9 * max(np.abs(gref).max(), 1e-6)
+    assert dH == pytest.approx(ref[-1], rel=1e-9, abs=1e-12)
+    assert cav.observables()["step"] == steps
+
+
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f64", 1e-12)])
 def test_register_budgets_agree(storage, tol):
     """Both builds of the transposed collision, and the size-based choice, on
