@@ -43,18 +43,6 @@ namespace {
 
 constexpr int kRB = 256;
 
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialisation is scheduled as its predecessor's blocks exit, before that
-// grid's completion is signalled; it waits here for the completion (and the
-// memory flush) before touching global memory.  Without the launch attribute
-// the wait is a no-op.  Every thread of every kernel below waits before any
-// global access or early return, so each grid completes only after its
-// predecessor did and the chain stays ordered.  No kernel triggers its
-// successor early (griddepcontrol.launch_dependents): at 256 x 256 an early
-// trigger, before or after the wait, made the whole adjoint 6-20% slower,
-// the wait alone 3% faster than plain stream order.
-__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 template <typename C>
 __device__ __forceinline__ void load19(const C* __restrict__ b, int64_t plane, int64_t off,
                                        C (&f)[9], C (&gf)[5], C (&gs)[5]) {
@@ -86,7 +74,7 @@ __global__ void __launch_bounds__(256) k_step_record(const C* __restrict__ src,
                                                      int nx, int ny, int64_t pitch,
                                                      int64_t plane, int write_macros,
                                                      C* __restrict__ pre_out) {
-  chain_wait();
+  grid_dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -101,7 +89,7 @@ __global__ void __launch_bounds__(256) k_collide_pre(const C* __restrict__ pre,
                                                      const C* __restrict__ phi,
                                                      const NodeParams<C> P, int nx, int ny,
                                                      int64_t pitch, int64_t plane) {
-  chain_wait();
+  grid_dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -210,7 +198,7 @@ __global__ void __launch_bounds__(256) k_adj_seed(const C* __restrict__ SN, C* _
                                                   C* __restrict__ wphib, const NodeParams<C> P,
                                                   int nx, int ny, int64_t pitch, int64_t plane,
                                                   C inv_dT) {
-  chain_wait();
+  grid_dep_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * ny) return;
   const int y = t >> 1, x = 1 + (t & 1);
@@ -261,7 +249,7 @@ __global__ void __launch_bounds__(256, (kCapped && sizeof(C) == 4) ? 4 : 1)
                                                   C* __restrict__ wphib, const NodeParams<C> P,
                                                   int nx, int ny, int64_t pitch, int64_t plane,
                                                   int fold, const C* __restrict__ S_prev) {
-  chain_wait();
+  grid_dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -364,7 +352,7 @@ __global__ void k_sum_partials(const double* __restrict__ part, int n, double* _
 template <typename C>
 __global__ void __launch_bounds__(256) k_copy19(const C* __restrict__ src, C* __restrict__ dst,
                                                 int64_t n) {
-  chain_wait();
+  grid_dep_wait();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     dst[k] = src[k];
@@ -417,22 +405,12 @@ struct SegGraph {
   }
 };
 
-// Launch with programmatic stream serialisation when the previous operation
-// on the stream (or in the capture) is one of the kernels above.
+// Every kernel above waits in grid_dep_wait(): launched chained to its
+// predecessor on the stream when that is one of them.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_chained(bool chained, void (*k)(KArgs...), dim3 grid, dim3 block,
                            cudaStream_t s, Args... args) {
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cfg.attrs = at;
-  cfg.numAttrs = chained ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k, args...);
+  return launch_kernel(chained, k, grid, block, 0, s, args...);
 }
 
 // Two events for a fork and a join between streams (no timing).

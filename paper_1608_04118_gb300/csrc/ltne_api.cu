@@ -419,8 +419,10 @@ LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
   return a;
 }
 
-cudaError_t launch_step(ltne_handle* h, int src_buf, int write_macros, cudaStream_t st) {
-  const LatticeArgs a = lattice_args(h, src_buf, write_macros);
+cudaError_t launch_step(ltne_handle* h, int src_buf, int write_macros, cudaStream_t st,
+                        bool chained = false) {
+  LatticeArgs a = lattice_args(h, src_buf, write_macros);
+  a.chained = chained ? 1 : 0;
   switch (h->p.storage) {
     case LTNE_F64: return launch_step_f64(a, h->P, h->shape, st);
     case LTNE_F32: return launch_step_f32(a, h->P, h->shape, st);
@@ -451,7 +453,7 @@ cudaError_t build_graph(ltne_handle* h, int parity) {
   int b = parity;
   cudaError_t le = cudaSuccess;
   for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
-    le = launch_step(h, b, 0, h->cap_stream);
+    le = launch_step(h, b, 0, h->cap_stream, k > 0);
     b ^= 1;
   }
   cudaGraph_t g = nullptr;
@@ -752,14 +754,16 @@ int ltne_step(ltne_handle* h, int64_t n) {
     h->step += kGraphSteps;
     h->launches += kGraphSteps;
   }
+  bool chained = false;  // the stream's last operation is a step kernel of this call
   for (; plain > 0; --plain) {
-    e = launch_step(h, h->cur, 0, h->stream);
+    e = launch_step(h, h->cur, 0, h->stream, chained);
     if (e != cudaSuccess) return fail_cuda(e);
+    chained = true;
     h->cur ^= 1;
     ++h->step;
     ++h->launches;
   }
-  e = launch_step(h, h->cur, 1, h->stream);
+  e = launch_step(h, h->cur, 1, h->stream, chained);
   if (e != cudaSuccess) return fail_cuda(e);
   h->cur ^= 1;
   ++h->step;

@@ -39,7 +39,39 @@ struct LatticeArgs {
   void* um_out;             // |u| plane written for the next state
   int* err;                 // device error word: set by a bounded wait that gave up
   int slab_walls;           // BC_SLAB: which of the first / last rows are walls
+  int chained;              // launch as a programmatic dependent of the stream's last kernel
 };
+
+// Programmatic dependent launch.  A kernel launched with programmatic
+// stream serialisation is scheduled as the blocks of the kernel before it
+// on the stream exit, before that grid's completion is signalled, and waits
+// here for the completion (and its memory flush) before touching global
+// memory; without the launch attribute the wait is a no-op.  Every thread
+// of a kernel that may be launched so executes it before any global access
+// or early return, so each grid completes only after its predecessor did.
+// No kernel triggers its dependents early (griddepcontrol.launch_dependents):
+// blocks of the next kernel parked on the SMs while a single-wave grid still
+// runs made the adjoint's chain 6-20 % slower at 256 x 256.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch k with the programmatic-serialisation attribute when `chained`.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(bool chained, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t s, Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // Launch configuration of the step kernel: a block of bx x by threads,
 // each advancing one node or (pair = 1, FP32 arithmetic only, at most

@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(kPairMaxThreads, kPairMinBlocks) k_step_pair(
     const int ny, const int64_t pitch, const int64_t plane, const float scale,
     const float inv_scale, const int write_macros, const uint32_t* __restrict__ tick_in,
     uint32_t* __restrict__ tick_out, const float* __restrict__ um_in, float* __restrict__ um_out) {
+  grid_dep_wait();
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t tick = read_tick<S, float>(tick_in, tick_out);
@@ -343,10 +344,11 @@ cudaError_t launch_step_pair_t(const LatticeArgs& a, const NodeParams<double>& P
   float* mac = static_cast<float*>(a.mac);
   const float* um_in = static_cast<const float*>(a.um_in);
   float* um_out = static_cast<float*>(a.um_out);
+  cudaError_t e;
 #define LTNE_PAIR_LAUNCH(bc)                                                                   \
-  k_step_pair<S, bc><<<grid, block, 0, st>>>(src, dst, phi, mac, P, P1, a.nx, a.ny, a.pitch,   \
-                                             a.plane, scale, inv_scale, a.write_macros,        \
-                                             a.tick_in, a.tick_out, um_in, um_out)
+  e = launch_kernel(a.chained != 0, k_step_pair<S, bc>, grid, block, 0, st, src, dst, phi,     \
+                    mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,                \
+                    a.write_macros, a.tick_in, a.tick_out, um_in, um_out)
   switch (a.bc) {
     case BC_CAVITY: LTNE_PAIR_LAUNCH(BC_CAVITY); break;
     case BC_PERIODIC: LTNE_PAIR_LAUNCH(BC_PERIODIC); break;
@@ -354,6 +356,7 @@ cudaError_t launch_step_pair_t(const LatticeArgs& a, const NodeParams<double>& P
     default: return cudaErrorInvalidValue;
   }
 #undef LTNE_PAIR_LAUNCH
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
                                               uint32_t* __restrict__ tick_out,
                                               const C* __restrict__ um_in,
                                               C* __restrict__ um_out, const int slab_walls) {
+  grid_dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t tick = read_tick<S, C>(tick_in, tick_out);
@@ -290,33 +291,34 @@ cudaError_t launch_step_t(const LatticeArgs& a, const NodeParams<double>& Pd, St
   C* mac = static_cast<C*>(a.mac);
   const C* um_in = static_cast<const C*>(a.um_in);
   C* um_out = static_cast<C*>(a.um_out);
+  const bool ch = a.chained != 0;
+  const dim3 g = grid, b = block;
+  cudaError_t e;
   switch (a.bc) {
     case BC_CAVITY:
-      k_step<S, C, BC_CAVITY><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny, a.pitch,
-                                                      a.plane, scale, inv_scale, a.write_macros,
-                                                      a.tick_in, a.tick_out, um_in, um_out, 0);
+      e = launch_kernel(ch, k_step<S, C, BC_CAVITY>, g, b, 0, st, src, dst, phi, mac, P, a.nx,
+                        a.ny, a.pitch, a.plane, scale, inv_scale, a.write_macros, a.tick_in,
+                        a.tick_out, um_in, um_out, 0);
       break;
     case BC_PERIODIC:
-      k_step<S, C, BC_PERIODIC><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
-                                                        a.pitch, a.plane, scale, inv_scale,
-                                                        a.write_macros, a.tick_in, a.tick_out,
-                                                        um_in, um_out, 0);
+      e = launch_kernel(ch, k_step<S, C, BC_PERIODIC>, g, b, 0, st, src, dst, phi, mac, P, a.nx,
+                        a.ny, a.pitch, a.plane, scale, inv_scale, a.write_macros, a.tick_in,
+                        a.tick_out, um_in, um_out, 0);
       break;
     case BC_CHANNEL:
-      k_step<S, C, BC_CHANNEL><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny,
-                                                       a.pitch, a.plane, scale, inv_scale,
-                                                       a.write_macros, a.tick_in, a.tick_out,
-                                                       um_in, um_out, 0);
+      e = launch_kernel(ch, k_step<S, C, BC_CHANNEL>, g, b, 0, st, src, dst, phi, mac, P, a.nx,
+                        a.ny, a.pitch, a.plane, scale, inv_scale, a.write_macros, a.tick_in,
+                        a.tick_out, um_in, um_out, 0);
       break;
     case BC_SLAB:
-      k_step<S, C, BC_SLAB><<<grid, block, 0, st>>>(src, dst, phi, mac, P, a.nx, a.ny, a.pitch,
-                                                    a.plane, scale, inv_scale, a.write_macros,
-                                                    a.tick_in, a.tick_out, um_in, um_out,
-                                                    a.slab_walls);
+      e = launch_kernel(ch, k_step<S, C, BC_SLAB>, g, b, 0, st, src, dst, phi, mac, P, a.nx,
+                        a.ny, a.pitch, a.plane, scale, inv_scale, a.write_macros, a.tick_in,
+                        a.tick_out, um_in, um_out, a.slab_walls);
       break;
     default:
       return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
