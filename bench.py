@@ -630,7 +630,7 @@ def main():
         host_out = {}
         barrier()
         t0 = time.perf_counter()
-        cav.set_fields(porosity=phi)  # H2D of the porosity and the initial fields
+        cav.set_fields(porosity=phi)  # H2D of the porosity; the fields at rest, T = T_ref
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         cav.step(k)
@@ -642,8 +642,10 @@ def main():
         t3 = time.perf_counter()
         te = t3 - t0
         tt = max_over_ranks(te, dev)
-        h2d = phi.nbytes + 5 * nodes * 4  # porosity + five staged fields (compute type)
-        d2h = 5 * nodes * 4 + 18 * 8      # five fields + the observables accumulators
+        # bytes the copies move: the porosity plane in the compute type (the
+        # initial fields are the defaults, zero deviations set on the device)
+        h2d = nodes * esz
+        d2h = 5 * nodes * esz + 18 * 8    # five fields + the observables accumulators
         e2e = {"value": whole_job_mlups(nodes, k, ws, tt), "unit": UNIT,
                "h2d_bytes_per_step": h2d / k, "d2h_bytes_per_step": d2h / k,
                "note": "whole run through the C ABI: set_fields from host arrays, %d steps, "

@@ -6,7 +6,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <unistd.h>
+
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -48,26 +54,94 @@ bool in_open(double v, double lo, double hi) { return v > lo && v < hi && isfini
 // handles chunk c = [lo, hi).  The chunking does not depend on the core
 // count, so per-chunk partial results combine identically on any host.
 constexpr int kHostChunks = 64;
+
+// Worker threads kept for the life of the process (one per host core but
+// the caller's), started at the first large pass: a pass hands out its
+// chunks through an atomic counter to the workers and the calling thread
+// and returns when all are done.  Thread creation per pass cost about as
+// much as the conversions of a staged block.  A pass that finds the pool
+// busy (another thread's pass), or runs in a process forked after the
+// pool started, runs on the calling thread alone.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool pool;
+    return pool;
+  }
+  // fn(c) for every c in [0, n); false if the pool could not take the pass
+  bool run(int n, const std::function<void(int)>& fn) {
+    if (getpid() != pid_ || workers_.empty()) return false;
+    std::unique_lock<std::mutex> busy(run_m_, std::try_to_lock);
+    if (!busy.owns_lock()) return false;
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      job_ = &fn;
+      n_ = n;
+      next_.store(0);
+      active_ = (int)workers_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (int c; (c = next_.fetch_add(1)) < n;) fn(c);
+    std::unique_lock<std::mutex> lk(m_);
+    done_.wait(lk, [&] { return active_ == 0; });
+    job_ = nullptr;
+    return true;
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : workers_)
+      if (t.joinable()) t.join();
+  }
+
+ private:
+  HostPool() : pid_(getpid()) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nt = (int)std::min<unsigned>(hw ? hw : 1, kHostChunks);
+    for (int t = 1; t < nt; ++t) workers_.emplace_back([this] { work(); });
+  }
+  void work() {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(int)>* job;
+      int n;
+      {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        job = job_;
+        n = n_;
+      }
+      for (int c; (c = next_.fetch_add(1)) < n;) (*job)(c);
+      std::lock_guard<std::mutex> lk(m_);
+      if (--active_ == 0) done_.notify_one();
+    }
+  }
+  const pid_t pid_;
+  std::vector<std::thread> workers_;
+  std::mutex run_m_, m_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* job_ = nullptr;
+  std::atomic<int> next_{0};
+  int n_ = 0, active_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
 template <typename F>
 void host_chunks(int64_t n, F fn) {
   const int64_t len = (n + kHostChunks - 1) / kHostChunks;
-  auto run = [&](int first, int stride) {
-    for (int c = first; c < kHostChunks; c += stride) {
-      const int64_t lo = (int64_t)c * len, hi = std::min(n, lo + len);
-      if (lo < hi) fn(c, lo, hi);
-    }
+  auto chunk = [&](int c) {
+    const int64_t lo = (int64_t)c * len, hi = std::min(n, lo + len);
+    if (lo < hi) fn(c, lo, hi);
   };
-  const unsigned hw = std::thread::hardware_concurrency();
-  const int nt = n < ((int64_t)1 << 18) ? 1 : (int)std::min<unsigned>(hw ? hw : 1, kHostChunks);
-  if (nt <= 1) {
-    run(0, 1);
-    return;
-  }
-  std::vector<std::thread> pool;
-  pool.reserve(nt - 1);
-  for (int t = 1; t < nt; ++t) pool.emplace_back(run, t, nt);
-  run(0, nt);
-  for (auto& th : pool) th.join();
+  if (n >= ((int64_t)1 << 18) && HostPool::get().run(kHostChunks, chunk)) return;
+  for (int c = 0; c < kHostChunks; ++c) chunk(c);
 }
 
 // Pinned staging of whole fields between host arrays and the device planes:
@@ -504,8 +578,10 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
     if (ez != cudaSuccess) return fail_cuda(ez);
   }
 
-  // Stage the fields as deviations (rho - 1, ux, uy, T - T_ref; compute
-  // type) into the macro planes, then k_init.
+  // Stage the given fields as deviations (rho - 1, ux, uy, T - T_ref;
+  // compute type) into the macro planes, then k_init.  A field not given
+  // takes its default (rho = 1, u = 0, T = T_ref), a zero deviation: the
+  // zeroed plane already holds it, and nothing is staged or copied.
   const double defaults[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
   const double refs[5] = {1.0, 0.0, 0.0, p.T_ref, p.T_ref};
   const double* src[5] = {rho, ux, uy, T_f, T_s};
@@ -531,6 +607,7 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
     });
   };
   for (int k = 0; k < 5; ++k) {
+    if (!src[k]) continue;
     rc = stage(src[k], defaults[k], refs[k], h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
     if (rc != LTNE_OK) return rc;
   }
