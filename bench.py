@@ -235,6 +235,25 @@ def cpu_baseline_oracle(n, target_s=12.0):
             "c1_64x64_1e4_steps_s": dt_c1}
 
 
+def cpu_baseline_reduced(phys, m, steps):
+    """CPU-baseline leg of the reduced-storage line: the FP64 oracle, timed
+    on the host cores, on the down-sized parity run (m x m, `steps` steps of
+    the same physics); its fields and observables are the reference the
+    line's per-field errors are taken against."""
+    import oracle
+    from oracle import Oracle, OracleParams
+
+    o = Oracle(OracleParams.make(m, m, **phys)).init()
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cpu = {"value": m * m * steps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": "FP64 oracle, %dx%d cavity with the same physics, %d steps (%.1f s)"
+                     % (m, m, steps, dt)}
+    return cpu, o.macros(), o.observables()
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle, as it stands, on the host cores."""
     ws, rank, _ = dist_env()
@@ -360,8 +379,6 @@ def run_reduced(args):
 
     B.build()
     from paper_1608_04118_gb300.ltne import Cavity
-    import oracle
-    from oracle import Oracle, OracleParams
 
     c = W.C5_REDUCED
     phys = {k: c[k] for k in ("Ra", "Pr", "Da", "porosity", "H", "gamma_sf", "sigma", "T_hot",
@@ -391,8 +408,7 @@ def run_reduced(args):
             del cav
             torch.cuda.empty_cache()
     m = c["parity_n"]
-    o = Oracle(OracleParams.make(m, m, **phys)).init().step(c["steps"])
-    ref, robs = o.macros(), o.observables()
+    cpu, ref, robs = cpu_baseline_reduced(phys, m, c["steps"])
     errors = {}
     for st in ("f32", "f16", "bf16"):
         # the schedule the MLUPS above were measured with
@@ -423,7 +439,7 @@ def run_reduced(args):
             "roofline": {st: {"achieved": bpl[st] * rates[st] * 1e6 / 1e9, "peak": peak,
                               "frac": bpl[st] * rates[st] * 1e6 / 1e9 / peak, "unit": "GB/s",
                               "peak_kind": kind} for st in rates},
-            "errors_vs_fp64_oracle": errors, "oracle_cores": oracle.num_threads()}
+            "errors_vs_fp64_oracle": errors, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
