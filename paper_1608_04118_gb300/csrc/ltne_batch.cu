@@ -79,12 +79,13 @@ __device__ __forceinline__ void tile_nodes(const float* __restrict__ src, float*
         step_pair<float, BC_CAVITY>(s, o, nullptr, m, K.P2, x0, y, d.nx, d.ny,
                                     (uint32_t)d.pitch, (uint32_t)d.plane, 1.0f, 1.0f,
                                     write_macros, 0u, nullptr, nullptr);
-      } else {  // a wall node in the pair, or the last node of an odd row
+      } else if (x0 + 1 < d.nx) {  // a wall column in the pair
+        step_pair_side<float>(s, o, nullptr, m, K.P2, x0, y, d.nx, d.ny, (uint32_t)d.pitch,
+                              (uint32_t)d.plane, 1.0f, 1.0f, write_macros, 0u, nullptr,
+                              nullptr);
+      } else {  // the last node of an odd row
         step_node<float, float, BC_CAVITY>(s, o, nullptr, m, K.P, x0, y, d.nx, d.ny, d.pitch,
                                            d.plane, 1.0f, 1.0f, write_macros, 0u);
-        if (x0 + 1 < d.nx)
-          step_node<float, float, BC_CAVITY>(s, o, nullptr, m, K.P, x0 + 1, y, d.nx, d.ny,
-                                             d.pitch, d.plane, 1.0f, 1.0f, write_macros, 0u);
       }
     }
   }

@@ -293,6 +293,87 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
                  gs);
 }
 
+// A cavity pair holding a left or right wall node (x0 = 0, or x0 + 1 =
+// nx - 1).  The wall node is rebuilt from the interior node next to it,
+// which is the pair's other node: both lanes pull around that node (one
+// scalar pull, broadcast), its macroscopic values give the non-equilibrium
+// extrapolation, and the lanes that are wall nodes take the rebuild -- the
+// side wall node at its wall temperature, the other lane too on a
+// bottom/top row (adiabatic: the neighbour's temperatures).  Then both
+// lanes continue as any pair.  The same rebuild as the one-node step, in
+// paired arithmetic, without the warp divergence of two one-node steps
+// beside the pairs of the rest of the row.
+template <typename S>
+__device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __restrict__ dst,
+                                               const float* __restrict__ phi_field,
+                                               float* __restrict__ mac, const NodeParams<F2>& P,
+                                               const int x0, const int y, const int nx,
+                                               const int ny, const uint32_t pi, const uint32_t pl,
+                                               const float scale, const float inv_scale,
+                                               const int write_macros, const uint32_t tick,
+                                               const float* __restrict__ um_in,
+                                               float* __restrict__ um_out) {
+  const bool left = x0 == 0;
+  const bool wall_row = y == 0 || y == ny - 1;
+  const int cx = left ? 1 : nx - 2;
+  const int cy = y == 0 ? 1 : (y == ny - 1 ? ny - 2 : y);
+  float fs[9], gfs[5], gss[5];
+  Pops<S, float>::pull(src, (int64_t)pi, (int64_t)pl, cx, cx - 1, cx + 1, cy, cy - 1, cy + 1,
+                       inv_scale, fs, gfs, gss);
+  F2 f[9], gf[5], gs[5];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = F2(fs[i], fs[i]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    gf[i] = F2(gfs[i], gfs[i]);
+    gs[i] = F2(gss[i], gss[i]);
+  }
+  const uint32_t noff = (uint32_t)cy * pi + (uint32_t)cx;
+  Medium<F2> mdn = P.um;
+  if (phi_field) {
+    const float pn = phi_field[noff];
+    mdn = medium_at<F2>(P, F2(pn, pn));
+  }
+  if (P.hv_local) {
+    const float un = um_in[noff];
+    set_exchange<F2>(mdn, hv_local_at<F2>(P, F2(un, un)));
+  }
+  Macro<F2> mn;
+  macros<F2>(P, mdn, f, gf, gs, mn);
+  // wall temperatures: the side wall's in the wall lane, the neighbour's
+  // (adiabatic rows) in the other
+  const float side = left ? P.dT_hot.v.x : P.dT_cold.v.x;
+  F2 twf = mn.dTf, tws = mn.dTs;
+  if (left) {
+    twf.v.x = side;
+    tws.v.x = side;
+  } else {
+    twf.v.y = side;
+    tws.v.y = side;
+  }
+  F2 rf[9], rgf[5], rgs[5];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) rf[i] = f[i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    rgf[i] = gf[i];
+    rgs[i] = gs[i];
+  }
+  nee<F2>(P, mn, twf, tws, rf, rgf, rgs);
+  const bool wx = left || wall_row, wy = !left || wall_row;
+  auto pick = [&](F2 r, F2 v) { return F2(wx ? r.v.x : v.v.x, wy ? r.v.y : v.v.y); };
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = pick(rf[i], f[i]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    gf[i] = pick(rgf[i], gf[i]);
+    gs[i] = pick(rgs[i], gs[i]);
+  }
+  const uint32_t off = (uint32_t)y * pi + (uint32_t)x0;
+  finish_pair<S>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out, f, gf,
+                 gs);
+}
+
 // Register budget of the pair kernel: blocks of at most 128 threads and at
 // least 5 resident per SM, i.e. at most 102 registers (it compiles to 96
 // without spilling) and 20 warps per SM.  Uncapped it takes about 110, and
@@ -319,6 +400,9 @@ __global__ void __launch_bounds__(kPairMaxThreads, kPairMinBlocks) k_step_pair(
   if (uniform) {
     step_pair<S, BC>(src, dst, phi_field, mac, P, x0, y, nx, ny, (uint32_t)pitch,
                      (uint32_t)plane, scale, inv_scale, write_macros, tick, um_in, um_out);
+  } else if (BC == BC_CAVITY && full) {
+    step_pair_side<S>(src, dst, phi_field, mac, P, x0, y, nx, ny, (uint32_t)pitch,
+                      (uint32_t)plane, scale, inv_scale, write_macros, tick, um_in, um_out);
   } else {
     step_node<S, float, BC>(src, dst, phi_field, mac, P1, x0, y, nx, ny, pitch, plane, scale,
                             inv_scale, write_macros, tick, nullptr, um_in, um_out);

@@ -195,13 +195,12 @@ __global__ void __launch_bounds__(TX * TY, kPairMinBlocks) k_step_tma(
     } else if (x0 > 0 && x0 + 2 < nx) {  // both nodes on a wall row
       step_pair<S, BC_CAVITY>(src, dst, phi_field, mac, P, x0, y, nx, ny, pi, pl, scale,
                               inv_scale, write_macros, tick, um_in, um_out);
-    } else {  // a wall column in the pair, or the last node of an odd row
+    } else if (x0 + 1 < nx) {  // a wall column in the pair
+      step_pair_side<S>(src, dst, phi_field, mac, P, x0, y, nx, ny, pi, pl, scale, inv_scale,
+                        write_macros, tick, um_in, um_out);
+    } else {  // the last node of an odd row
       step_node<S, float, BC_CAVITY>(src, dst, phi_field, mac, P1, x0, y, nx, ny, pitch, plane,
                                      scale, inv_scale, write_macros, tick, nullptr, um_in, um_out);
-      if (x0 + 1 < nx)
-        step_node<S, float, BC_CAVITY>(src, dst, phi_field, mac, P1, x0 + 1, y, nx, ny, pitch,
-                                       plane, scale, inv_scale, write_macros, tick, nullptr, um_in,
-                                       um_out);
     }
   }
 }
