@@ -206,10 +206,11 @@ int64_t ltne_launch_count(const ltne_handle* h);
    row in paired FP32 arithmetic (FP32, FP16 and BF16 storage only, and
    block_x * block_y <= 128).  The schedule changes no result beyond FP32
    rounding: the arithmetic per node is the same, and for a given
-   nodes_per_thread the block shape changes no bit.  Defaults, for lattices
-   of 2^20 nodes or more: 32 x 4 with two nodes per thread (FP16, BF16),
-   128 x 1 with two (FP32), 128 x 2 with one (FP64); smaller lattices:
-   128 x 2 with one.  May be called at any time between steps.
+   nodes_per_thread the block shape changes no bit.  Defaults: 32 x 4 with
+   two nodes per thread for FP16 / BF16 lattices of 2^20 nodes or more,
+   128 x 1 with two for FP32 lattices of 2^22 nodes or more, 128 x 2 with
+   one otherwise (and always for FP64).  May be called at any time between
+   steps.
    LTNE_ERR_INVALID_ARG for other schedules. */
 int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
                       int32_t nodes_per_thread);

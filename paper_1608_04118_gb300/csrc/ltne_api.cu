@@ -774,21 +774,22 @@ int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
     return rc;
   }
   layout(h);
-  // Default schedules, the fastest measured on GB300: from 2^20 nodes up,
-  // two nodes per thread in 32 x 4 blocks for 16-bit storage (issue-bound
-  // in the one-node form) and in 128 x 1 blocks for FP32 (at the HBM
-  // roofline either way); one node per thread in 128 x 2 blocks for FP64
-  // and for smaller lattices, whose steps are a single wave bound by the
-  // latency of one thread's work (the 256 cavities of 64..512 nodes a side
-  // ran one by one at 32.2 GLUPS with one node per thread, 23.4 with two).
-  const bool large = (int64_t)p->nx * p->ny >= ((int64_t)1 << 20);
-  if (!large) {
-    // 128 x 2, one node per thread
-  } else if (p->storage == LTNE_F16DEV || p->storage == LTNE_BF16DEV) {
+  // Default schedules, the fastest measured on GB300: two nodes per thread
+  // in 32 x 4 blocks for 16-bit storage from 2^20 nodes up (issue-bound in
+  // the one-node form: 43.4 against 41.9 GLUPS at 1024^2 FP16), in 128 x 1
+  // blocks for FP32 from 2^22 nodes up (at the HBM roofline either way;
+  // below, one node per thread is faster: 39.5 against 37.3 GLUPS at
+  // 1024^2, equal at 2048^2); one node per thread in 128 x 2 blocks for
+  // FP64 and for smaller lattices, whose steps are a single wave or a few,
+  // bound by the latency of one thread's work (the 256 cavities of 64..512
+  // nodes a side ran one by one at 32.2 GLUPS with one node per thread,
+  // 23.4 with two).
+  const int64_t nodes = (int64_t)p->nx * p->ny;
+  if ((p->storage == LTNE_F16DEV || p->storage == LTNE_BF16DEV) && nodes >= ((int64_t)1 << 20)) {
     h->shape.bx = 32;
     h->shape.by = 4;
     h->shape.pair = 1;
-  } else if (p->storage == LTNE_F32) {
+  } else if (p->storage == LTNE_F32 && nodes >= ((int64_t)1 << 22)) {
     h->shape.bx = 128;
     h->shape.by = 1;
     h->shape.pair = 1;

@@ -170,12 +170,15 @@ def test_option_validation_without_gpu(lt):
     lt.ltne_destroy(h)
     # step schedules: default per storage type; two nodes per thread need
     # float arithmetic and at most 128 threads per block
-    for storage, default in ((lt.LTNE_F32, (128, 1, 2)), (lt.LTNE_F16DEV, (32, 4, 2)),
-                             (lt.LTNE_BF16DEV, (32, 4, 2)), (lt.LTNE_F64, (128, 2, 1))):
-        h = lt.ltne_create(lt.ltne_default_params(1024, 1024, storage=storage))
-        assert lt.ltne_get_schedule(h) == default  # 2^20 nodes: the large-lattice default
+    for storage, default, side in ((lt.LTNE_F32, (128, 1, 2), 2048),
+                                   (lt.LTNE_F16DEV, (32, 4, 2), 1024),
+                                   (lt.LTNE_BF16DEV, (32, 4, 2), 1024),
+                                   (lt.LTNE_F64, (128, 2, 1), 1024)):
+        # the large-lattice default from side^2 nodes (2^22 FP32, 2^20 16-bit)
+        h = lt.ltne_create(lt.ltne_default_params(side, side, storage=storage))
+        assert lt.ltne_get_schedule(h) == default
         lt.ltne_destroy(h)
-        h = lt.ltne_create(lt.ltne_default_params(1024, 1023, storage=storage))
+        h = lt.ltne_create(lt.ltne_default_params(side, side - 1, storage=storage))
         assert lt.ltne_get_schedule(h) == (128, 2, 1)
         lt.ltne_destroy(h)
         h = lt.ltne_create(lt.ltne_default_params(32, 32, storage=storage))
