@@ -390,7 +390,7 @@ def run_reduced(args):
         for one_node in (False, True):
             cav = Cavity(n, n, stream=stream, storage=st, **phys)
             if one_node:
-                cav.set_schedule(128, 2, 1)
+                cav.set_schedule(64, 2, 1)
             schedules[(st, one_node)] = cav.schedule
             cav.set_fields()
             with torch.cuda.stream(stream):
@@ -588,7 +588,7 @@ def main():
                  porosity_field=1, **kw)
     if args.block or args.npt:
         bx, by = ((int(v) for v in args.block.split(",")) if args.block
-                  else ((128, 2) if args.npt == 1 else (128, 1)))
+                  else ((64, 2) if args.npt == 1 else (128, 1)))
         cav.set_schedule(bx, by, args.npt or cav.schedule[2])
     schedule = cav.schedule
     cav.set_fields(porosity=phi)

@@ -208,7 +208,7 @@ int64_t ltne_launch_count(const ltne_handle* h);
    rounding: the arithmetic per node is the same, and for a given
    nodes_per_thread the block shape changes no bit.  Defaults: 32 x 4 with
    two nodes per thread for FP16 / BF16 lattices of 2^20 nodes or more,
-   128 x 1 with two for FP32 lattices of 2^22 nodes or more, 128 x 2 with
+   128 x 1 with two for FP32 lattices of 2^22 nodes or more, 64 x 2 with
    one otherwise (and always for FP64).  May be called at any time between
    steps.
    LTNE_ERR_INVALID_ARG for other schedules. */

@@ -779,11 +779,11 @@ int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
   // the one-node form: 43.4 against 41.9 GLUPS at 1024^2 FP16), in 128 x 1
   // blocks for FP32 from 2^22 nodes up (at the HBM roofline either way;
   // below, one node per thread is faster: 39.5 against 37.3 GLUPS at
-  // 1024^2, equal at 2048^2); one node per thread in 128 x 2 blocks for
-  // FP64 and for smaller lattices, whose steps are a single wave or a few,
-  // bound by the latency of one thread's work (the 256 cavities of 64..512
-  // nodes a side ran one by one at 32.2 GLUPS with one node per thread,
-  // 23.4 with two).
+  // 1024^2, equal at 2048^2); one node per thread in 64 x 2 blocks for FP64
+  // and for smaller lattices, whose steps are a single wave or a few, bound
+  // by the latency of one thread's work (64 x 2 against 128 x 2: 40.5
+  // against 38.3 GLUPS at 512^2 FP32, 34.2 against 32.2 FP16, equal at
+  // 256^2 and in FP64).
   const int64_t nodes = (int64_t)p->nx * p->ny;
   if ((p->storage == LTNE_F16DEV || p->storage == LTNE_BF16DEV) && nodes >= ((int64_t)1 << 20)) {
     h->shape.bx = 32;
@@ -1037,7 +1037,7 @@ int ltne_step_slabs(ltne_handle* h, int32_t nslabs, int64_t n, void* scratch, si
                     1, pitch, ec, st);
     if (e != cudaSuccess) return fail_cuda(e);
   }
-  StepShape one;  // one node per thread, 128 x 2
+  StepShape one;  // one node per thread, 64 x 2
   int b = 0;
   for (int64_t k = 0; k < n && e == cudaSuccess; ++k) {
     for (const SlabGeom& s : g) {

@@ -78,7 +78,7 @@ cudaError_t launch_kernel(bool chained, void (*k)(KArgs...), dim3 grid, dim3 blo
 // kPairBlockThreads threads per block) two neighbouring nodes of a row.
 constexpr int kPairBlockThreads = 128;
 struct StepShape {
-  int bx = 128;
+  int bx = 64;
   int by = 2;
   int pair = 0;
   int tma = 0;  // two nodes per thread from TMA-staged tiles (cavity walls only)

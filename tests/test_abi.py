@@ -173,16 +173,16 @@ def test_option_validation_without_gpu(lt):
     for storage, default, side in ((lt.LTNE_F32, (128, 1, 2), 2048),
                                    (lt.LTNE_F16DEV, (32, 4, 2), 1024),
                                    (lt.LTNE_BF16DEV, (32, 4, 2), 1024),
-                                   (lt.LTNE_F64, (128, 2, 1), 1024)):
+                                   (lt.LTNE_F64, (64, 2, 1), 1024)):
         # the large-lattice default from side^2 nodes (2^22 FP32, 2^20 16-bit)
         h = lt.ltne_create(lt.ltne_default_params(side, side, storage=storage))
         assert lt.ltne_get_schedule(h) == default
         lt.ltne_destroy(h)
         h = lt.ltne_create(lt.ltne_default_params(side, side - 1, storage=storage))
-        assert lt.ltne_get_schedule(h) == (128, 2, 1)
+        assert lt.ltne_get_schedule(h) == (64, 2, 1)
         lt.ltne_destroy(h)
         h = lt.ltne_create(lt.ltne_default_params(32, 32, storage=storage))
-        assert lt.ltne_get_schedule(h) == (128, 2, 1)
+        assert lt.ltne_get_schedule(h) == (64, 2, 1)
         for bad in ((48, 2, 1), (16, 1, 1), (512, 1, 1), (128, 4, 1), (128, 2, 3), (128, 0, 1),
                     (64, 4, 2), (256, 1, 2)):
             assert lib.ltne_set_schedule(h, *bad) == lt.LTNE_ERR_INVALID_ARG, bad
