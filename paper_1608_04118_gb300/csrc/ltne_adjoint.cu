@@ -658,17 +658,20 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
                        bool chained) {
     const int64_t a = s * K, len = ((a + K < N) ? a + K : N) - a;
     cudaError_t le = cudaSuccess;
+    bool forked = false;
     if (s > 0) {
       le = cudaEventRecord(ev.fork, main_s);
       if (le == cudaSuccess) le = cudaStreamWaitEvent(aux, ev.fork, 0);
+      forked = le == cudaSuccess;
       if (le == cudaSuccess) le = recompute_body(aux, K, buf19(L.ckpt, s - 1), q ^ 1, false);
       chained = false;
     }
     if (le == cudaSuccess)
       le = reverse_body(main_s, len, q, s == L.nseg - 1, lL, lO, chained, s == 0);
-    if (s > 0 && le == cudaSuccess) {
-      le = cudaEventRecord(ev.join, aux);
-      if (le == cudaSuccess) le = cudaStreamWaitEvent(main_s, ev.join, 0);
+    if (forked) {  // the main stream waits for the recompute even after a failure
+      cudaError_t je = cudaEventRecord(ev.join, aux);
+      if (je == cudaSuccess) je = cudaStreamWaitEvent(main_s, ev.join, 0);
+      if (le == cudaSuccess) le = je;
     }
     return le;
   };
@@ -692,6 +695,7 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
           cudaError_t le = cudaGetLastError();
           if (le == cudaSuccess) le = cudaEventRecord(ev.fork, cs);
           if (le == cudaSuccess) le = cudaStreamWaitEvent(st2, ev.fork, 0);
+          const bool forked = le == cudaSuccess;
           // the recompute without its copy (the root)
           C* p0 = buf19(L.pops, 0);
           C* p1 = buf19(L.pops, 1);
@@ -708,8 +712,13 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
           C* lL = buf19(L.lam, lp);
           C* lO = buf19(L.lam, lp ^ 1);
           if (le == cudaSuccess) le = reverse_body(cs, K, q, false, lL, lO, false, false);
-          if (le == cudaSuccess) le = cudaEventRecord(ev.join, st2);
-          if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, ev.join, 0);
+          // rejoin the second stream even after a failed launch, so that the
+          // capture can end and leave it usable
+          if (forked) {
+            cudaError_t je = cudaEventRecord(ev.join, st2);
+            if (je == cudaSuccess) je = cudaStreamWaitEvent(cs, ev.join, 0);
+            if (le == cudaSuccess) le = je;
+          }
           return le;
         });
       if (e != cudaSuccess) break;
