@@ -776,7 +776,8 @@ int ltne_create(const ltne_params* p, void* cuda_stream, ltne_handle** out) {
   layout(h);
   // Default schedules, the fastest measured on GB300: two nodes per thread
   // in 32 x 4 blocks for 16-bit storage from 2^20 nodes up (issue-bound in
-  // the one-node form: 43.4 against 41.9 GLUPS at 1024^2 FP16), in 128 x 1
+  // the one-node form: 43.5 against 42.8 GLUPS at 1024^2 FP16, 47.9 against
+  // 43.5 at 2048^2; 35.1 against 38.6 at 724^2), in 128 x 1
   // blocks for FP32 from 2^22 nodes up (at the HBM roofline either way;
   // below, one node per thread is faster: 39.5 against 37.3 GLUPS at
   // 1024^2, equal at 2048^2); one node per thread in 64 x 2 blocks for FP64
