@@ -276,10 +276,10 @@ size_t ltne_adjoint_workspace_bytes(const ltne_handle* h, int64_t n_steps, int32
 
 /* Register budget of the adjoint's transposed-collision kernel (no
    counterpart in the paper).  LTNE_ADJ_ONE_WAVE: every register the kernel
-   wants (119 per thread in FP32), for lattices whose grid fits one wave of
+   wants (123 per thread in FP32), for lattices whose grid fits one wave of
    the device, where a reverse step's time is one thread's latency;
-   LTNE_ADJ_CAPPED: registers capped so that four blocks of 256 threads
-   share an SM (FP32; a few values spill to local memory), for larger
+   LTNE_ADJ_CAPPED: registers capped at 64 so that 1024 threads share an SM
+   (FP32; a few values spill to local memory), for larger
    lattices, where occupancy hides the latency.  LTNE_ADJ_AUTO (default)
    picks by the lattice size.  The two builds run the same code; they agree
    to rounding (under the cap the compiler may contract a different set of

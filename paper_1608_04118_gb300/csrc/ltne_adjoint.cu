@@ -234,10 +234,10 @@ __global__ void __launch_bounds__(256) k_adj_seed(const C* __restrict__ SN, C* _
 // R2: transposed streaming (gather from y + e_i) and transposed collision;
 // a wall node's thread then folds its result (R1) unless S_n is the initial
 // state (fold = 0), whose wall nodes were not rebuilt.  The fold raises the
-// kernel's registers (119 against 73 without it, FP32).  Two builds of the
+// kernel's registers (123 against 73 without it, FP32).  Two builds of the
 // same code: kCapped = false keeps them all (lattices that fit one wave,
 // where the kernel's time is one thread's latency); kCapped = true caps them
-// so that four blocks share an SM (FP32; larger lattices, where occupancy
+// at 64, 1024 threads' worth per SM (FP32; larger lattices, where occupancy
 // hides the latency), spilling a few values to local memory.
 template <typename C, bool kCapped>
 __global__ void __launch_bounds__(256, (kCapped && sizeof(C) == 4) ? 4 : 1)

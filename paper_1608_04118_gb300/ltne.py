@@ -401,7 +401,7 @@ class Cavity:
 
     def set_adjoint_schedule(self, mode):
         """Register budget of the adjoint's transposed collision: 0 by lattice
-        size, 1 all registers (one wave), 2 capped (four blocks per SM)."""
+        size, 1 all registers (one wave), 2 capped (64 registers)."""
         ltne_set_adjoint_schedule(self.h, mode)
         return self
 
