@@ -1,6 +1,7 @@
-"""The benchmark's multi-rank path (one independent cavity per rank, no
-data-path collective): max-over-ranks timing and the whole-job value, run as
-two gloo ranks on the CPU."""
+"""The benchmark's host-side logic without a GPU: the multi-rank path (one
+independent cavity per rank, no data-path collective: max-over-ranks timing
+and the whole-job value, run as two gloo ranks on the CPU), the reference
+arm's JSON line and the CPU-baseline object."""
 import os
 import socket
 
@@ -48,3 +49,33 @@ def test_single_process_is_identity():
 
     assert bench.max_over_ranks(3.25) == 3.25
     assert bench.whole_job_mlups(100, 10, 1, 2.0) == pytest.approx(100 * 10 / 2.0 / 1e6)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference: the FP64 oracle on the host cores, one JSON
+    line with the reference keys (a small lattice, two steps)."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "64",
+                        "--steps", "2", "--warmup", "1"], cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_reports_one_core_and_the_small_configuration():
+    import bench
+
+    cpu = bench.cpu_baseline_oracle(64, target_s=0.2)
+    assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1
+    assert cpu["one_core"]["value"] > 0
+    assert cpu["c1_64x64_1e4_steps_s"] > 0
