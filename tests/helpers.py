@@ -43,3 +43,19 @@ def field_errors(gpu, orc):
                 Ts=rel_l2(gpu["Ts"], orc["Ts"]),
                 rho=rel_l2(gpu["rho"] - 1.0, orc["rho"] - 1.0),
                 rho_abs=float(np.abs(gpu["rho"] - orc["rho"]).max()))
+
+
+def golden(name):
+    """The "name = value" lines of tests/golden/<name>.txt as floats (the
+    values the paper prints; each file cites its passage)."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + ".txt")
+    out = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = (t.strip() for t in line.split("=", 1))
+                out[k] = float(v)
+    return out

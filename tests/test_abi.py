@@ -74,10 +74,16 @@ def test_struct_layout_matches_header(lt, name):
 
 
 def test_defaults_follow_section4(lt):
+    """The relaxation rates, the thermal weight parameter and the viscosity
+    ratio default to the paper's Sec. 4 values (tests/golden); T_ref
+    defaults to the mean wall temperature."""
+    from tests.helpers import golden
+
+    g = golden("sec4_parameters")
     p = lt.ltne_default_params(64, 64)
-    assert (p.s_e, p.s_eps, p.s_q) == (1.1, 1.1, 1.2)
-    assert (p.zeta_e, p.zeta_nu, p.eta_e, p.eta_nu) == (1.1, 1.1, 1.1, 1.1)
-    assert p.varpi == 0.4 and p.J_e == 1.0 and p.T_ref == 0.5
+    for k in ("s_e", "s_eps", "s_q", "zeta_e", "zeta_nu", "eta_e", "eta_nu", "varpi", "J_e"):
+        assert getattr(p, k) == g[k], k
+    assert p.T_ref == 0.5
 
 
 def _create(lt, **kw):

@@ -10,8 +10,12 @@ import pytest
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-PAPER = dict(Pr=1.0, Da=1e-4, porosity=0.8, gamma_sf=1000.0, sigma=1.0, J_e=1.0, T_hot=11.0,
-             T_cold=1.0, T_ref=1.0, F_phi=0.068, hv_local=1, Dp_over_L=0.0135)
+from tests.helpers import golden
+
+G = golden("sec4_parameters")
+PAPER = dict({k: G[k] for k in ("Pr", "Da", "porosity", "gamma_sf", "sigma", "J_e", "T_hot",
+                                "T_cold", "T_ref", "F_phi", "Dp_over_L")}, hv_local=1)
+RESULT = golden("sec4_max_dtheta")
 
 
 def _steady_dtheta(Ra, n, steps):
@@ -25,7 +29,8 @@ def _steady_dtheta(Ra, n, steps):
     assert ob["residual"] < 1e-4  # steady (FP32 round-off floor)
     f = c.fields()
     y0, y1 = (n - 1) // 2, n // 2  # mid-height, between the two middle rows for even n
-    dtheta = 0.5 * ((f["Ts"][y0] - f["Tf"][y0]) + (f["Ts"][y1] - f["Tf"][y1])) / 10.0
+    dT = PAPER["T_hot"] - PAPER["T_cold"]
+    dtheta = 0.5 * ((f["Ts"][y0] - f["Tf"][y0]) + (f["Ts"][y1] - f["Tf"][y1])) / dT
     return float(np.abs(dtheta).max())
 
 
@@ -34,6 +39,6 @@ def test_max_solid_fluid_difference_about_ten_percent_at_ra_1e9():
         pytest.skip("no CUDA device")
     d6 = _steady_dtheta(1e6, 128, 150_000)
     d8 = _steady_dtheta(1e8, 192, 400_000)
-    d9 = _steady_dtheta(1e9, 192, 700_000)
+    d9 = _steady_dtheta(RESULT["Ra"], int(RESULT["n"]), 700_000)
     assert d6 < d8 < d9
-    assert 0.08 <= d9 <= 0.12, d9
+    assert RESULT["band_lo"] <= d9 <= RESULT["band_hi"], d9
