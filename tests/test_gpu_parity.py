@@ -138,6 +138,39 @@ def test_graph_replay_is_bitwise_equal_to_single_steps():
     assert a.launches == b.launches == 100
 
 
+def test_handles_on_concurrent_host_threads():
+    """Two lattices large enough for the host worker pool (set_fields with
+    all fields given, steps, get_fields), driven from two host threads at
+    once, give the bits of the same runs done one after the other: a pass
+    that finds the pool busy runs on its own thread."""
+    import threading
+
+    nx, ny = 640, 600
+    cfgs = [W.random_params(90 + k, nx, ny) for k in range(2)]
+    fields = [W.random_fields(nx, ny, 190 + k) for k in range(2)]
+    phis = [W.porosity_field(nx, ny, 0.4, 0.9, seed=290 + k).reshape(-1) for k in range(2)]
+
+    def run(k, out):
+        torch.cuda.set_device(0)
+        c = cavity_for(cfgs[k], storage="f32", phi=phis[k])
+        for _ in range(3):
+            c.set_fields(porosity=phis[k], **fields[k]).step(40)
+            out[k] = c.fields()
+        c.close()
+
+    seq, par = {}, {}
+    for k in range(2):
+        run(k, seq)
+    ts = [threading.Thread(target=run, args=(k, par)) for k in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for k in range(2):
+        for f in seq[k]:
+            assert np.array_equal(seq[k][f], par[k][f]), (k, f)
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
 def test_checkpoint_resume_bitwise(storage):
     cfg = W.random_params(10, 48, 40)
