@@ -623,6 +623,7 @@ def main():
     per_launch = t / args.steps
     peak, peak_kind = load_peaks()
     achieved = BYTES_PER_LUP[args.storage] * nodes / per_launch / 1e9
+    traffic = kernel_traffic(args.storage, n, schedule[2])
     ob = cav.observables()
     # the FP64 observables reduction (one ltne_observables call: two kernels,
     # the 18-value readback and the host finish), median of 5
@@ -689,7 +690,9 @@ def main():
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "frac_of_8TBs": achieved / 8000.0,
                      "bytes_per_lup": BYTES_PER_LUP[args.storage],
-                     "traffic": kernel_traffic(args.storage, n, schedule[2]),
+                     "traffic": traffic,
+                     # the ncu-counted bytes of one launch over the launch time
+                     "achieved_dram": None if traffic is None else traffic / per_launch / 1e9,
                      "kernel": "%s<%s> (one launch = one step of %d nodes)"
                                % ("k_step_pair" if schedule[2] == 2 else "k_step", args.storage,
                                   nodes)},
