@@ -634,7 +634,7 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   return LTNE_OK;
 }
 
-int reduce_handle(ltne_handle* h, double* acc) {
+int reduce_launch(ltne_handle* h) {
   const ltne_params& p = h->p;
   ReduceArgs a;
   a.mac = h->ws + h->off_mac;
@@ -653,11 +653,15 @@ int reduce_handle(ltne_handle* h, double* acc) {
   a.update_prev = 1;
   a.blocks = h->red_blocks;
   a.is_double = h->ec == 8;
-  cudaError_t e = launch_reduce(a, h->stream);
-  if (e != cudaSuccess) return fail_cuda(e);
-  e = cudaMemcpyAsync(acc, a.out, NACC * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-  if (e != cudaSuccess) return fail_cuda(e);
-  e = cudaStreamSynchronize(h->stream);
+  return fail_cuda(launch_reduce(a, h->stream));
+}
+
+int reduce_handle(ltne_handle* h, double* acc) {
+  const int rc = reduce_launch(h);
+  if (rc != LTNE_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(acc, h->ws + h->off_out, NACC * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return fail_cuda(e);
 }
 
@@ -854,16 +858,31 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   if (!h || !out) return LTNE_ERR_INVALID_ARG;
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;
-  double acc[NACC];
-  const int rr = reduce_handle(h, acc);
+  cudaError_t e = cudaSuccess;
+  if (!h->pin_obs) {
+    e = cudaHostAlloc(reinterpret_cast<void**>(&h->pin_obs), (NACC + 1) * sizeof(double),
+                      cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      h->pin_obs = nullptr;
+      return fail_cuda(e);
+    }
+  }
+  const int rr = reduce_launch(h);
   if (rr != LTNE_OK) return rr;
-  // a staged step that gave up waiting for its tile reports here (the
-  // fields are then not trustworthy); the word is cleared
-  int err = 0;
-  cudaError_t e = cudaMemcpyAsync(&err, h->ws + h->off_tick + 2 * sizeof(uint32_t), sizeof(err),
-                                  cudaMemcpyDeviceToHost, h->stream);
+  // the accumulators and the device error word in one read-back: a staged
+  // step that gave up waiting for its tile reports here (the fields are then
+  // not trustworthy); the word is cleared
+  int* errp = reinterpret_cast<int*>(h->pin_obs + NACC);
+  e = cudaMemcpyAsync(h->pin_obs, h->ws + h->off_out, NACC * sizeof(double),
+                      cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(errp, h->ws + h->off_tick + 2 * sizeof(uint32_t), sizeof(int),
+                        cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail_cuda(e);
+  double acc[NACC];
+  for (int k = 0; k < NACC; ++k) acc[k] = h->pin_obs[k];
+  const int err = *errp;
   if (err) {
     e = cudaMemsetAsync(h->ws + h->off_tick + 2 * sizeof(uint32_t), 0, sizeof(err), h->stream);
     return e == cudaSuccess ? LTNE_ERR_TIMEOUT : fail_cuda(e);
@@ -1112,6 +1131,7 @@ void ltne_destroy(ltne_handle* h) {
   if (!h) return;
   drop_graphs(h);
   release_pinned(h);
+  if (h->pin_obs) cudaFreeHost(h->pin_obs);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   delete h;

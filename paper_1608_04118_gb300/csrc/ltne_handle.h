@@ -36,6 +36,9 @@ struct ltne_handle {
   // two pinned host buffers that stage whole fields in and out (allocated
   // at the first set_fields / get_fields, freed by ltne_destroy)
   char* pin[2] = {nullptr, nullptr};
+  // pinned landing place of the observables' accumulators and the device
+  // error word (one asynchronous read-back per ltne_observables call)
+  double* pin_obs = nullptr;
   cudaEvent_t pin_ev[2] = {nullptr, nullptr};
   size_t pin_bytes = 0;
 };
@@ -47,4 +50,7 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
                     const double* uy, const double* T_f, const double* T_s, void* pre_out);
 // The handle's observables reduction into acc[NACC] (synchronises).
 int reduce_handle(ltne_handle* h, double* acc);
+// The same reduction, enqueued on the handle's stream only (the result in
+// the workspace's output slot).
+int reduce_launch(ltne_handle* h);
 }  // namespace ltne
