@@ -492,3 +492,140 @@ def test_correction_term_removes_the_unwanted_flux(Pr):
     F_over_phi_sum = A * N
     assert drift[0] == pytest.approx(-c * F_over_phi_sum, rel=0.15)
     assert abs(drift[1]) <= 0.15 * c * F_over_phi_sum
+
+
+# ---------------------------------------------------------------- f1 -----
+def _hv_by_hand(u, nu, Pr, L, Dp_over_L):
+    """h_v / (rho c)_f of Eq. 52 written out from the paper's definitions:
+    H_p = h_v D_p^2 / k_f = 0.376 Re^0.644 Pr^0.37, Re = u_m D_p / nu_f,
+    D_p = (D_p / L) L, and h_v / (rho c)_f = H_p alpha_f / D_p^2 with
+    alpha_f = nu_f / Pr."""
+    Dp = Dp_over_L * L
+    Re = u * Dp / nu
+    Hp = 0.376 * Re ** 0.644 * Pr ** 0.37
+    return Hp * (nu / Pr) / Dp ** 2
+
+
+@pytest.mark.parametrize("u,Pr,Dp_over_L,phi,sigma", [
+    (0.05, 0.7, 0.0135, 0.6, 1.0),
+    (0.02, 0.7, 0.0135, 0.6, 1.0),
+    (0.05, 3.0, 0.0135, 0.45, 2.0),
+    (0.03, 1.0, 0.05, 0.8, 0.5)])
+def test_local_exchange_coefficient_eq52_uniform_flow(u, Pr, Dp_over_L, phi, sigma):
+    """Eq. 52 in a uniform periodic box moving at a constant |u| (no force:
+    permeability so large that the Darcy drag is below FP64 resolution, no
+    Forchheimer term, no buoyancy): the local h_v is the same at every node
+    and every step, so T_f - T_s follows the trapezoid law of Eqs. 41-46,
+    D^{n+1} (1 + k/2) = D^n (1 - k/2), with k = a + b = h_v/(rho c)_f
+    (1/phi + 1/((1 - phi) sigma)) and h_v from Eq. 52 computed here by hand.
+    Four cases vary |u|, Pr, D_p and the phase weights, so a wrong
+    exponent, D_p, Pr factor or length scale changes k."""
+    nx = ny = 4
+    nu, L = 0.05, 100.0
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=0.0, nu_override=nu, Pr=Pr,
+                                 Da=1e300, F_phi=0.0, porosity=phi, sigma=sigma, gamma_sf=2.0,
+                                 hv_local=1, Dp_over_L=Dp_over_L, L_ref=L, T_hot=0.5,
+                                 T_cold=0.5))
+    ang = 0.3
+    n = nx * ny
+    o.init(ux=np.full(n, u * np.cos(ang)), uy=np.full(n, u * np.sin(ang)), Tf=np.full(n, 0.8),
+           Ts=np.full(n, 0.3))
+    hv = _hv_by_hand(u, nu, Pr, L, Dp_over_L)
+    k = hv / phi + hv / ((1 - phi) * sigma)
+    assert 1e-3 < k < 1.0  # the exchange is resolved and the law is non-trivial
+    r = (1 - k / 2) / (1 + k / 2)
+    mac = o.macros()
+    D0 = mac["Tf"][0, 0] - mac["Ts"][0, 0]
+    # the temperature solve of S_0 already used this k: A_f - A_s = D (1 + k/2)
+    gf, gs = o.get_pops()[1:]
+    assert gf[0, 0].sum() - gs[0, 0].sum() == pytest.approx(D0 * (1 + k / 2), rel=1e-13)
+    for step in range(1, 30):
+        o.step(1)
+        mac = o.macros()
+        assert np.allclose(np.hypot(mac["ux"], mac["uy"]), u, rtol=1e-13)
+        assert np.allclose(mac["Tf"] - mac["Ts"], D0 * r ** step, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- p13' ---
+@pytest.mark.parametrize("varpi", [0.4, 0.6])
+def test_fluid_diffusivity_chapman_enskog(varpi):
+    """A sine mode of T_f with u = 0 and H = 0 decays at alpha_f k^2, with
+    alpha_f = c_sT^2 (1/zeta_alpha - 1/2) (Eq. 49, c_sT^2 = varpi/2) and
+    alpha_f = nu_f / Pr computed here from the inputs.  The solid phase is
+    given a diffusivity 12.5 times smaller (gamma_sf / sigma = 0.08), so a
+    fluid phase relaxed with the solid-phase rates (Eq. 40 in place of
+    Eq. 39) decays far too slowly, and the solid mode, started equal, must
+    decay at alpha_s k^2 alongside."""
+    nx, ny = 128, 3
+    nu, Pr, gsf, sig = 0.1, 2.0, 0.2, 2.5
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=0.0, nu_override=nu, Pr=Pr, H=0.0,
+                                 gamma_sf=gsf, sigma=sig, varpi=varpi))
+    alpha_f = nu / Pr
+    alpha_s = gsf / sig * alpha_f
+    x = np.arange(nx)
+    k = 2 * np.pi / nx
+    T = 0.5 + 0.1 * np.sin(k * x)
+    o.init(Tf=np.tile(T, ny), Ts=np.tile(T, ny))
+
+    def amps():
+        m = o.macros()
+        return [2 * np.mean((m[key][1] - 0.5) * np.sin(k * x)) for key in ("Tf", "Ts")]
+
+    o.step(200)
+    a1 = amps()
+    o.step(1800)
+    a2 = amps()
+    rate_f = -np.log(a2[0] / a1[0]) / 1800
+    rate_s = -np.log(a2[1] / a1[1]) / 1800
+    assert rate_f == pytest.approx(alpha_f * k * k, rel=1e-3)
+    assert rate_s == pytest.approx(alpha_s * k * k, rel=1e-3)
+
+
+# ---------------------------------------------------------------- rates --
+def test_relaxation_rates_act_on_their_moments():
+    """Eq. 17 and Eqs. 39-40 place each relaxation rate on one moment.  In a
+    spatially uniform periodic state streaming moves equal values between
+    equal nodes, so only the collision acts: with u = 0, no force and no
+    exchange (H = 0), the non-equilibrium part of every non-conserved moment
+    is multiplied by (1 - rate) per step (Eq. 10; Eqs. 32-33), the conserved
+    moments stay put.  Every rate is distinct here, and the hydrodynamic ones
+    are computed from the inputs by Eqs. 23 and 49, so a rate on the wrong
+    moment, a wrong varpi in c_sT^2 or in the (-4 + 5 varpi) entry of
+    Eqs. 37-38, or a mix-up of the two phases' rates fails."""
+    ex, ey, w, M, Mi, N, Ni = _e()
+    nu, Je, Pr, gsf, sig, varpi = 0.07, 1.3, 0.8, 3.0, 1.4, 0.55
+    rates = dict(s_e=0.7, s_eps=1.3, s_q=1.6, zeta_e=0.9, zeta_nu=1.5, eta_e=1.25, eta_nu=0.6)
+    nx = ny = 3
+    o = Oracle(OracleParams.make(nx, ny, bc=BC_PERIODIC, Ra=0.0, nu_override=nu, J_e=Je, Pr=Pr,
+                                 H=0.0, gamma_sf=gsf, sigma=sig, varpi=varpi, porosity=0.55,
+                                 **rates))
+    s_nu = 1 / (3 * Je * nu + 0.5)                       # Eq. 23, c_s^2 = 1/3
+    csT2 = varpi / 2                                      # Eq. 49
+    zeta_a = 1 / ((nu / Pr) / csT2 + 0.5)
+    eta_a = 1 / ((gsf / sig * nu / Pr) / csT2 + 0.5)
+    s = np.array([0, rates["s_e"], rates["s_eps"], 0, rates["s_q"], 0, rates["s_q"], s_nu, s_nu])
+    qf = np.array([0, zeta_a, zeta_a, rates["zeta_e"], rates["zeta_nu"]])
+    qs = np.array([0, eta_a, eta_a, rates["eta_e"], rates["eta_nu"]])
+    rho, Tf, Ts = 1.02, 0.7, 0.35
+    c3 = -4 + 5 * varpi
+    meq = np.array([rho, -2 * rho, rho, 0, 0, 0, 0, 0, 0])        # Eq. 15 at u = 0
+    nfeq = np.array([Tf, 0, 0, c3 * Tf, 0])                      # Eq. 37 at u = 0
+    nseq = np.array([Ts, 0, 0, c3 * Ts, 0])                      # Eq. 38
+    dm = np.array([0, 0.011, -0.007, 0, 0.004, 0, -0.003, 0.006, -0.005])
+    dnf = np.array([0, 0.012, -0.009, 0.02, -0.015])
+    dns = np.array([0, -0.008, 0.011, -0.013, 0.017])
+    f0 = np.linalg.solve(M, meq + dm)
+    gf0 = np.linalg.solve(N, nfeq + dnf)
+    gs0 = np.linalg.solve(N, nseq + dns)
+    nn = nx * ny
+    o.set_pops(np.tile(f0, nn), np.tile(gf0, nn), np.tile(gs0, nn))
+    for step in range(1, 6):
+        o.step(1)
+        f, gf, gs = o.get_pops()
+        for node in range(nn):
+            y, x = divmod(node, nx)
+            assert np.allclose(M @ f[y, x] - meq, dm * (1 - s) ** step, rtol=1e-12, atol=1e-15)
+            assert np.allclose(N @ gf[y, x] - nfeq, dnf * (1 - qf) ** step, rtol=1e-12,
+                               atol=1e-15)
+            assert np.allclose(N @ gs[y, x] - nseq, dns * (1 - qs) ** step, rtol=1e-12,
+                               atol=1e-15)
