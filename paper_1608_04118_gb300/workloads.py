@@ -76,11 +76,24 @@ def random_fields(nx, ny, seed, du=0.01, dT=0.3):
                 T_s=0.5 + dT * rng.uniform(-1, 1, n))
 
 
+RATE_KEYS = ("s_e", "s_eps", "s_q", "zeta_e", "zeta_nu", "eta_e", "eta_nu")
+
+
 def random_params(seed, nx, ny):
-    """Random but stable cavity parameters for brute-force parity."""
+    """Random but stable cavity parameters for brute-force parity.  The
+    non-hydrodynamic relaxation rates (s_e, s_eps, s_q of Eq. 17; zeta_e,
+    zeta_nu, eta_e, eta_nu of Eqs. 39-40) are drawn independently in
+    [0.8, 1.9] and varpi in [0.2, 0.8], so that a rate applied to the wrong
+    moment, or a varpi-dependent constant taken at the default 2/5, changes
+    the result."""
     rng = np.random.default_rng(seed)
-    return dict(nx=nx, ny=ny, Ra=float(10 ** rng.uniform(3, 5)), Pr=float(rng.uniform(0.7, 2)),
-                Da=float(10 ** rng.uniform(-3, -1)), porosity=float(rng.uniform(0.35, 0.9)),
-                H=float(10 ** rng.uniform(0, 3)), gamma_sf=float(10 ** rng.uniform(-1, 1.5)),
-                sigma=float(rng.uniform(0.5, 2)), J_e=float(rng.uniform(0.8, 1.5)),
-                T_hot=1.0, T_cold=0.0, T_ref=0.5, Ma=0.1)
+    d = dict(nx=nx, ny=ny, Ra=float(10 ** rng.uniform(3, 5)), Pr=float(rng.uniform(0.7, 2)),
+             Da=float(10 ** rng.uniform(-3, -1)), porosity=float(rng.uniform(0.35, 0.9)),
+             H=float(10 ** rng.uniform(0, 3)), gamma_sf=float(10 ** rng.uniform(-1, 1.5)),
+             sigma=float(rng.uniform(0.5, 2)), J_e=float(rng.uniform(0.8, 1.5)),
+             T_hot=1.0, T_cold=0.0, T_ref=0.5, Ma=0.1)
+    rr = np.random.default_rng([seed, 7])  # a second stream: the draws above are unchanged
+    for k in RATE_KEYS:
+        d[k] = float(rr.uniform(0.8, 1.9))
+    d["varpi"] = float(rr.uniform(0.2, 0.8))
+    return d

@@ -32,7 +32,7 @@ def _batch(cavs):
     from paper_1608_04118_gb300.ltne import Batch
 
     keys = ("nx", "ny", "Ra", "Pr", "Da", "porosity", "H", "gamma_sf", "sigma", "J_e", "T_hot",
-            "T_cold", "T_ref", "Ma")
+            "T_cold", "T_ref", "Ma", "varpi") + W.RATE_KEYS
     return Batch([{k: c[k] for k in keys if k in c} for c in cavs])
 
 
