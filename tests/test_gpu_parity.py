@@ -202,8 +202,18 @@ def test_nonfinite_is_reported():
     assert a.observables(allow_nonfinite=True)["nonfinite"] > 0
 
 
-@pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", 1e-2)])
-def test_reduced_storage_64_cavity_10k_steps(storage, tol):
+# The reduced-storage target is rel-L2 <= 1e-3 for u, T_f and T_s; it is
+# applied to the wall Nusselt numbers too.  BF16 cannot meet it with
+# deviations from the rest equilibrium: a single stochastic rounding of the
+# exact state already carries 1.2e-3 into j/rho (tests/test_storage_floor.py),
+# so its cases assert the target and are expected to fail.
+BF16_FLOOR = ("BF16 deviations from the rest equilibrium cannot reach 1e-3 in u: one "
+              "stochastic rounding of the exact state already puts 1.2e-3 into j/rho")
+RED = pytest.mark.xfail(strict=True, reason=BF16_FLOOR)
+
+
+@pytest.mark.parametrize("storage", ["f16", pytest.param("bf16", marks=RED)])
+def test_reduced_storage_64_cavity_10k_steps(storage):
     """FP16 / BF16 deviation storage (stochastic rounding) with FP32
     arithmetic on the 64 x 64 cavity after 10^4 steps, against the oracle."""
     cfg = W.C1_PLAIN_64
@@ -211,13 +221,13 @@ def test_reduced_storage_64_cavity_10k_steps(storage, tol):
     c = cavity_for(cfg, storage=storage).set_fields().step(cfg["steps"])
     err = field_errors(c.fields(), o.macros())
     for k in ("u", "Tf", "Ts"):
-        assert err[k] <= tol, (storage, k, err)
+        assert err[k] <= 1e-3, (storage, k, err)
 
 
 @pytest.mark.parametrize("schedule", [(128, 2, 1), (32, 4, 2)])
-@pytest.mark.parametrize("storage,tol_u,tol_T,tol_nu", [("f32", 1e-5, 1e-5, 1e-4),
-                                                        ("f16", 1e-3, 1e-3, 2e-3),
-                                                        ("bf16", 6e-3, 2e-3, 2e-2)])
+@pytest.mark.parametrize("storage,tol_u,tol_T,tol_nu", [
+    ("f32", 1e-5, 1e-5, 1e-4), ("f16", 1e-3, 1e-3, 1e-3),
+    pytest.param("bf16", 1e-3, 1e-3, 1e-3, marks=RED)])
 def test_reduced_storage_512_parity_run(storage, tol_u, tol_T, tol_nu, schedule):
     """Physics of the reduced-storage configuration (Ra 1e6, H 1000, phi 0.6,
     Da 1e-2) on the down-sized 512 x 512 cavity for 2000 steps: per-field
