@@ -55,8 +55,12 @@ enum {
 
 /* Population storage.  Compute is FP64 for LTNE_F64 and FP32 otherwise.
    Every form stores deviations from the rest equilibrium: f_i - w_i rho_0
-   and g_i - w~_i T_0 (rho_0 = 1, T_0 = T_ref); the 16-bit forms scale the
-   deviation by a power of two before rounding to nearest even. */
+   and g_i - w~_i T_0 (rho_0 = 1, T_0 = T_ref).  The 16-bit forms round
+   stochastically, not to nearest: the FP32 deviation (times 2^10 for FP16,
+   unscaled for BF16) gets random bits added below the kept fraction bits
+   before truncation (the paired conversion with random bits of sm_100 and
+   later), the bits drawn from a counter-based generator seeded by the node
+   and the step, so a run is reproducible bit for bit. */
 enum { LTNE_F64 = 0, LTNE_F32 = 1, LTNE_F16DEV = 2, LTNE_BF16DEV = 3 };
 
 /* Boundary modes.  CAVITY is the problem of Sec. 4; the other two are test
@@ -305,13 +309,13 @@ int ltne_adjoint(ltne_handle* h, const double* porosity, const double* rho, cons
 
 /* Observables of fields the caller holds on the device, allocating nothing.
    The paper has no counterpart: this serves callers that cannot allocate
-   device memory at the moment they need a reduction -- code running inside
-   CUDA graph capture (allocation is not allowed there), a framework whose
-   allocator is not reachable from the calling thread, a loop that must not
-   allocate.  Those callers can neither size nor bind a workspace, so the
-   reduction's per-block partial sums go to a fixed __device__ array inside
-   this library (590 KB, held by every GPU that loads the library until the
-   process exits).
+   device memory at the moment they need a reduction -- a plug-in or monitor
+   inside a host application that owns every device allocation and lends
+   none to its guests, a thread from which the framework's allocator is not
+   reachable, a real-time loop that must not allocate.  Those callers can
+   neither size nor bind a workspace, so the reduction's per-block partial
+   sums go to a fixed __device__ array inside this library (590 KB, held by
+   every GPU that loads the library until the process exits).
    fields: device, FP32, five planes of nx*ny values with row pitch `pitch`
      (>= nx) elements and plane stride pitch*ny, holding rho - 1, u_x, u_y,
      T_f - T_ref, T_s - T_ref (the layout ltne_get_fields() values map to).
@@ -326,11 +330,13 @@ int ltne_adjoint(ltne_handle* h, const double* porosity, const double* rho, cons
      device work.
    The first call on each device asks the runtime for the array's device
    address (cudaGetSymbolAddress, with that device current), so make one
-   call before any stream capture begins.  All calls share the array and it
-   keeps the last call's contents (every slot a call reads is written by that
-   call first): calls that overlap on the GPU -- on different streams, or on
-   one stream while another thread also calls -- race and give wrong
-   results.  Synchronises `cuda_stream`. */
+   call before any stream capture begins; a call that finds a different
+   context current on the device (after cudaDeviceReset) asks again.  All
+   calls share the array and it keeps the last call's contents (every slot
+   a call reads is written by that call first): calls that overlap on the
+   GPU -- on different streams, or on one stream while another thread also
+   calls -- race and give wrong results.  The call copies the result back
+   and synchronises `cuda_stream` before it returns. */
 int ltne_observables_static(const ltne_params* p, const float* fields, int64_t pitch,
                             const float* porosity, int64_t step, void* cuda_stream,
                             ltne_obs* out);

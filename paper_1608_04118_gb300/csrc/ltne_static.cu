@@ -4,12 +4,14 @@
 // workspace.
 //
 // Who needs it: code that can hand over field buffers but cannot allocate
-// device memory when it wants a reduction -- a monitor running inside CUDA
-// graph capture (allocation is not permitted while capturing), a host
-// framework whose allocator is not reachable from the calling thread, or a
-// real-time loop where an allocation (and the device synchronisation it may
-// imply) is not acceptable.
+// device memory when it wants a reduction -- a plug-in or monitor inside a
+// host application that owns every device allocation and offers none to its
+// guests, a thread from which the framework's allocator is not reachable, or
+// a real-time loop where an allocation (and the device synchronisation it
+// may imply) is not acceptable.
 #include <mutex>
+
+#include <cuda.h>
 
 #include "ltne.h"
 #include "ltne_internal.h"
@@ -28,24 +30,71 @@ __device__ __align__(256) double g_reduce_scratch[(kMaxBlocks + 1) * NACC];
 
 // Device address of g_reduce_scratch per device ordinal.  In host code the
 // symbol's name is only a stand-in: its device address must be asked for,
-// with the device current, before a kernel may be given it.
+// with the device current, before a kernel may be given it.  The address
+// belongs to the device's current (primary) context; after a
+// cudaDeviceReset() the next call finds a new context and asks again, so a
+// cached address never outlives the context it came from.
 constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;  // unique id of the context the address is for
+  double* ptr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
+
+// cuCtxGetCurrent and cuCtxGetId from the driver, fetched through the
+// runtime (no link-time dependence on the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+template <typename Fn>
+Fn driver_fn(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return reinterpret_cast<Fn>(p);
+  return nullptr;
+}
+
+// Unique id of the calling thread's current context; 0 when none is
+// current yet (the runtime creates the primary context on its first call
+// that needs one).
+cudaError_t current_context_id(unsigned long long* id) {
+  static const CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  if (!get_current || !get_id) return cudaErrorNotSupported;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  *id = 0;
+  if (!ctx) return cudaSuccess;
+  return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 cudaError_t scratch_for_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  unsigned long long id = 0;
+  e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchSlot& slot = g_scratch[dev];
+  if (!slot.ptr || id == 0 || slot.ctx_id != id) {
+    // first call on this device, or a context the cached address is not
+    // from: ask the runtime (which makes the primary context current if no
+    // context was), then record the context it answered for
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_reduce_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    if (id == 0) return cudaErrorDeviceUninitialized;
+    slot.ptr = static_cast<double*>(p);
+    slot.ctx_id = id;
   }
-  *out = g_scratch_ptr[dev];
+  *out = slot.ptr;
   return cudaSuccess;
 }
 

@@ -20,9 +20,16 @@
 // Every wait on an mbarrier is bounded: after kWaitSpins polls the block
 // records an error flag, waits once more (bounded) for its copies in flight,
 // and leaves; the host reports LTNE_ERR_TIMEOUT on the next observables call.
+// A copy can be neither cancelled nor waited for without limit, so if that
+// second wait gives up too, the block leaves with copies still in flight,
+// which may land in shared memory given to a later block of the same
+// launch: the error flag is already set, and the state of such a step is
+// reported invalid and must be discarded.
 #pragma once
 
 #include <cuda.h>
+
+#include <mutex>
 
 #include "ltne_pair.cuh"
 
@@ -212,17 +219,27 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 inline EncodeTiledFn encode_tiled_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  // initialised once, thread-safely (function-local static)
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return static_cast<EncodeTiledFn>(nullptr);
+  }();
   return fn;
 }
+
+// Launch facts of one staged-kernel instantiation on one device: the
+// dynamic shared memory attribute is set and the occupancy and SM count
+// are queried once per device, under a lock (host threads may launch on
+// several devices at once).
+struct TmaLaunchInfo {
+  int blocks_per_sm = 0, sms = 0;
+};
+constexpr int kTmaMaxDevices = 64;
 
 // Tensor map of a population buffer: dims (pitch, ny, 19 planes) of the
 // storage type, box (BW, BH, 19), zeros outside.
@@ -260,18 +277,29 @@ cudaError_t launch_tma_shape(const LatticeArgs& a, const NodeParams<double>& Pd,
   CUtensorMap map;
   cudaError_t e = make_tile_map<S, TX, TY>(&map, a.src, a.pitch, a.ny, a.plane);
   if (e != cudaSuccess) return e;
-  static int blocks_per_sm = 0, sms = 0;
-  if (!blocks_per_sm) {
-    int dev = 0, nb = 0;
-    if (cudaFuncSetAttribute(k_step_tma<S, TX, TY, NS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, B::kSmem) != cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<S, TX, TY, NS>, TX * TY,
-                                                      B::kSmem) != cudaSuccess ||
-        nb < 1)
-      return cudaErrorInvalidConfiguration;
-    blocks_per_sm = nb;
+  static TmaLaunchInfo info[kTmaMaxDevices];
+  static std::mutex mu;
+  int dev = 0, blocks_per_sm = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTmaMaxDevices)
+    return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    TmaLaunchInfo& li = info[dev];
+    if (!li.blocks_per_sm) {
+      int nb = 0, n_sm = 0;
+      if (cudaFuncSetAttribute(k_step_tma<S, TX, TY, NS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               B::kSmem) != cudaSuccess ||
+          cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<S, TX, TY, NS>, TX * TY,
+                                                        B::kSmem) != cudaSuccess ||
+          nb < 1)
+        return cudaErrorInvalidConfiguration;
+      li.sms = n_sm;
+      li.blocks_per_sm = nb;
+    }
+    blocks_per_sm = li.blocks_per_sm;
+    sms = li.sms;
   }
   const int ntiles = ((a.nx + B::W - 1) / B::W) * ((a.ny + B::H - 1) / B::H);
   const int grid = ntiles < blocks_per_sm * sms ? ntiles : blocks_per_sm * sms;

@@ -2,9 +2,9 @@
 
 ltne_observables_static() reduces fields that the caller already holds on
 the device, with its scratch in a fixed device array inside the library, so
-callers that cannot allocate device memory at that point (inside CUDA graph
-capture, without access to an allocator, in a loop that must not allocate)
-can still get the observables.  It must agree with ltne_observables(), which
+callers that cannot allocate device memory at that point (a plug-in whose
+host application owns every allocation, a thread without access to the
+allocator, a loop that must not allocate) can still get the observables.  It must agree with ltne_observables(), which
 uses the handle's workspace, and keep agreeing on later calls that reuse the
 same scratch.  This file is collected last so that a failure here comes after
 every other test has run.
@@ -75,8 +75,13 @@ def test_static_observables_rejects_lattices_beyond_its_scratch():
     from paper_1608_04118_gb300 import ltne as L
 
     fn = _entry(L)
-    p = L.ltne_default_params(16384, 16384)
     out = L.ltne_obs()
-    # rejected before any device work: the size check comes first
-    rc = fn(C.byref(p), C.c_void_p(256), 16384, None, 0, None, C.byref(out))
-    assert rc == L.LTNE_ERR_INVALID_ARG
+    # 8448 x 8192 passes every parameter check (its 19 population planes
+    # stay below 2^32 elements) but needs 33 x 128 = 4224 pass-1 blocks, more
+    # than the 4096 partial vectors of the fixed array; 8192 x 8192 (4096
+    # blocks) is the largest square served.  Rejected before any device
+    # work: the pointer is never dereferenced.
+    for nx, ny in ((8448, 8192), (8192, 8256), (16384, 16384)):
+        p = L.ltne_default_params(nx, ny)
+        rc = fn(C.byref(p), C.c_void_p(256), nx, None, 0, None, C.byref(out))
+        assert rc == L.LTNE_ERR_INVALID_ARG, (nx, ny)
