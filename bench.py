@@ -10,7 +10,13 @@ walls.  MLUPS = nodes x steps / seconds.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
-cavity (independent replicas, weak scaling) and rank 0 prints.
+cavity (independent replicas, weak scaling) and rank 0 prints.  At N = 1 the
+line also carries, under "forms", compact runs of the other forms next to
+the plain FP32 kernel: the 256-cavity batch (autotuned schedule), the
+forward + adjoint at 256 x 256 and the FP32 / FP16 / BF16 storage forms at
+8192 x 8192, each with its MLUPS, roofline fraction, errors against the
+oracle (whose timed run of the checked sample is that leg's CPU baseline)
+and the clocks sampled while it was timed (--no-forms skips them).
 """
 from __future__ import annotations
 
@@ -60,6 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the compact batched / adjoint / reduced-storage legs of the "
+                         "default line")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: single cavity (default, the headline line); c3: 256-cavity "
                          "batch; c4: forward + adjoint; c5: reduced-storage forms at 8192^2 "
@@ -254,6 +263,230 @@ def cpu_baseline_reduced(phys, m, steps):
     return cpu, o.macros(), o.observables()
 
 
+def _events_time(stream, fn, clocks_gpu=None):
+    """Run fn() (work enqueued on `stream`) between two CUDA events on that
+    stream; seconds, plus the clocks sampled meanwhile (None if not asked)."""
+    import torch
+
+    sampler = ClockSampler(clocks_gpu) if clocks_gpu is not None else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop() if sampler else None
+    return e0.elapsed_time(e1) / 1e3, clocks
+
+
+def _field_err(got, ref):
+    u = np.linalg.norm(np.stack([got["ux"] - ref["ux"], got["uy"] - ref["uy"]]))
+    u /= np.linalg.norm(np.stack([ref["ux"], ref["uy"]]))
+    return {"u": float(u), "Tf": float(np.linalg.norm(got["Tf"] - ref["Tf"])
+                                      / np.linalg.norm(ref["Tf"])),
+            "Ts": float(np.linalg.norm(got["Ts"] - ref["Ts"]) / np.linalg.norm(ref["Ts"]))}
+
+
+def form_batched(stream, plain_mlups, peak, gpu, steps=200, check_steps=100):
+    """Compact batched leg: the 256 cavities (seed 3) with the autotuned
+    schedule, `steps` timed steps; the plain FP32 kernel on the same
+    cavities one by one; errors of four cavities after `check_steps` steps
+    against the oracle, whose run of them is this leg's CPU baseline."""
+    import torch
+
+    import oracle
+    from oracle import Oracle, OracleParams
+    from paper_1608_04118_gb300.autotune import tune_batch
+    from paper_1608_04118_gb300.ltne import Batch, Cavity
+
+    cavs = W.batch_cavities(256, seed=3)
+    b = Batch(cavs, stream=stream)
+    sched, _, table = tune_batch(b, steps=4, warmup=2)
+    b.set_fields()
+    with torch.cuda.stream(stream):
+        b.step(3)
+    l0 = b.launches
+    t, clocks = _events_time(stream, lambda: b.step(steps), gpu)
+    launches = b.launches - l0
+    nodes = b.nodes
+    value = nodes * steps / t / 1e6
+    k_seq = 50
+    singles = []
+    for c in cavs:
+        cc = Cavity(c["nx"], c["ny"], stream=stream, storage="f32",
+                    **{k: v for k, v in c.items() if k not in ("nx", "ny")})
+        singles.append(cc.set_fields())
+    t_seq, _ = _events_time(stream, lambda: [cc.step(k_seq) for cc in singles])
+    for cc in singles:
+        cc.close()
+    seq = nodes * k_seq / t_seq / 1e6
+    # parity: four cavities of the batch against the oracle
+    idx = [int(i) for i in np.random.default_rng(30).choice(len(cavs), 4, replace=False)]
+    b.set_fields().step(check_steps)
+    errs, t_orc, n_orc = [], 0.0, 0
+    for i in idx:
+        c = cavs[i]
+        o = Oracle(OracleParams.make(c["nx"], c["ny"], **{k: v for k, v in c.items()
+                                                           if k not in ("nx", "ny")}))
+        t0 = time.perf_counter()
+        o.init().step(check_steps)
+        t_orc += time.perf_counter() - t0
+        n_orc += c["nx"] * c["ny"] * check_steps
+        errs.append(_field_err(b.fields(i), o.macros()))
+    b.close()
+    achieved = 152 * nodes * steps / t / 1e9
+    return {"mlups": value, "steps": steps, "nodes": nodes, "cavities": len(cavs),
+            "gpu_launches": int(launches),
+            "schedule": {"tile_x": sched[0], "tile_y": sched[1], "blocks": sched[2],
+                         "nodes_per_thread": sched[3], "trials": len(table)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "bytes_per_lup": 152},
+            "one_by_one_plain_fp32_mlups": seq, "vs_plain_fp32_one_by_one": value / seq,
+            "vs_plain_fp32_4096": value / plain_mlups,
+            "errors_vs_oracle": {"cavities": [{"index": i, "nx": cavs[i]["nx"],
+                                               "ny": cavs[i]["ny"], **e}
+                                              for i, e in zip(idx, errs)],
+                                 "steps": check_steps,
+                                 "max": {k: max(e[k] for e in errs) for k in ("u", "Tf", "Ts")},
+                                 "tolerance": 1e-5},
+            "cpu_baseline": {"value": n_orc / t_orc / 1e6, "unit": UNIT,
+                             "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "the four checked cavities, %d steps each (%.1f s)"
+                                       % (check_steps, t_orc)},
+            "clocks": clocks}
+
+
+def form_adjoint(stream, peak, gpu):
+    """Compact adjoint leg: forward 4000 steps + gradient of the hot-wall
+    Nusselt average by the reverse kernels with 64-step checkpoints at
+    256 x 256 (porosity U[0.4, 0.8] seed 4, Ra 1e5, Ergun mean Da 1e-3,
+    H 50), next to the plain FP32 forward of the same cavity; accuracy on a
+    20 x 16 cavity (120 steps) against the complex-step oracle, whose run is
+    this leg's CPU baseline."""
+    import math
+
+    import torch
+
+    import oracle
+    from oracle import ComplexOracle, OracleParams
+    from paper_1608_04118_gb300.ltne import Cavity, LTNE_K_ERGUN
+
+    c = W.C4_ADJOINT
+    nx, ny, steps = c["nx"], c["ny"], c["steps"]
+    seg = int(math.ceil(math.sqrt(steps)))
+    phi = W.porosity_field(nx, ny, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+    kw = {k: c[k] for k in ("Ra", "Pr", "Da", "H", "gamma_sf", "sigma", "T_hot", "T_cold",
+                            "T_ref")}
+    cav = Cavity(nx, ny, stream=stream, storage="f32", permeability=LTNE_K_ERGUN,
+                 porosity_field=1, **kw)
+    cav.adjoint(phi, 2 * seg, segment=seg)  # warm-up
+    out = {}
+    t, clocks = _events_time(stream, lambda: out.update(
+        r=cav.adjoint(phi, steps, segment=seg)), gpu)
+    J, g, dH = out["r"]
+    cav.set_fields(porosity=phi)
+    with torch.cuda.stream(stream):
+        cav.step(20)
+    t_fwd, _ = _events_time(stream, lambda: cav.step(steps))
+    cav.close()
+    nodes = nx * ny
+    # accuracy: the small cavity of the adjoint tests, FP32 gradient against
+    # complex-step derivatives of the oracle (12 interior nodes and H)
+    sm = dict(nx=20, ny=16, Ra=1e5, Pr=1.0, Da=1e-3, H=50.0, gamma_sf=3.0, sigma=1.2,
+              T_hot=1.0, T_cold=0.0, T_ref=0.5)
+    sphi = W.porosity_field(sm["nx"], sm["ny"], 0.4, 0.8, seed=44).reshape(-1)
+    nodes_k = W.fd_nodes(sm["nx"], sm["ny"], 12, seed=45)
+    p = OracleParams.make(sm["nx"], sm["ny"], ergun_K=1,
+                          **{k: v for k, v in sm.items() if k not in ("nx", "ny")})
+    ref = {}
+    t0 = time.perf_counter()
+    for k in list(nodes_k) + [-1]:
+        o = ComplexOracle(p, phi=sphi).perturb(int(k), 1e-30).init().step(120)
+        ref[int(k)] = o.objective()[1] / 1e-30
+    t_orc = time.perf_counter() - t0
+    sc = Cavity(sm["nx"], sm["ny"], stream=stream, storage="f32", permeability=LTNE_K_ERGUN,
+                porosity_field=1, **{k: v for k, v in sm.items() if k not in ("nx", "ny")})
+    _, gs, dHs = sc.adjoint(sphi, 120, segment=16)
+    sc.close()
+    gs = gs.double().cpu().numpy().reshape(-1)
+    gref = np.array([ref[int(k)] for k in nodes_k])
+    err_phi = float(np.abs(gs[nodes_k] - gref).max() / np.abs(gref).max())
+    err_H = float(abs(dHs - ref[-1]) / abs(ref[-1]))
+    plain = nodes * steps / t_fwd / 1e6
+    value = nodes * steps / t / 1e6
+    # algorithmic bytes per node-step: forward (156) + recompute (156) +
+    # reverse (read the recorded state 76, adjoint populations 152, dJ/dphi 8)
+    return {"mlups": value, "steps": steps, "segment": seg, "lattice": "%dx%d" % (nx, ny),
+            "plain_fp32_forward_mlups": plain, "vs_plain_fp32": value / plain,
+            "roofline": {"bound": "latency (one wave per reverse step at this size)",
+                         "achieved": 548 * value * 1e6 / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": 548 * value * 1e6 / 1e9 / peak, "bytes_per_lup": 548},
+            "J": J, "dJ_dH": dH, "max_abs_dJ_dphi": float(g.abs().max()),
+            "errors_vs_oracle": {"case": "20x16, 120 steps, FP32 adjoint vs complex step",
+                                 "dJ_dphi_max_rel": err_phi, "dJ_dH_rel": err_H,
+                                 "tolerance": 1e-3},
+            "cpu_baseline": {"value": sm["nx"] * sm["ny"] * 120 * len(ref) / t_orc / 1e6,
+                             "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle (complex step)",
+                             "sample": "%d complex-step runs of the 20x16 cavity, 120 steps "
+                                       "(%.1f s)" % (len(ref), t_orc)},
+            "clocks": clocks}
+
+
+def form_reduced(stream, plain_mlups, peak, gpu, steps=200):
+    """Compact reduced-storage leg: FP32 / FP16 / BF16 storage at 8192 x 8192
+    (phi 0.6, Da 1e-2, Ra 1e6, H 1000), default schedules, `steps` timed
+    steps each; per-field errors of the 512 x 512, 2000-step run against the
+    oracle, whose run is this leg's CPU baseline."""
+    import torch
+
+    from paper_1608_04118_gb300.ltne import Cavity
+
+    c = W.C5_REDUCED
+    phys = {k: c[k] for k in ("Ra", "Pr", "Da", "porosity", "H", "gamma_sf", "sigma", "T_hot",
+                              "T_cold", "T_ref")}
+    n = c["nx"]
+    rates, scheds, clocks, launches = {}, {}, {}, {}
+    for st in ("f32", "f16", "bf16"):
+        cav = Cavity(n, n, stream=stream, storage=st, **phys).set_fields()
+        scheds[st] = list(cav.schedule)
+        with torch.cuda.stream(stream):
+            cav.step(3)
+        l0 = cav.launches
+        t, clocks[st] = _events_time(stream, lambda: cav.step(steps), gpu)
+        launches[st] = int(cav.launches - l0)
+        rates[st] = n * n * steps / t / 1e6
+        cav.close()
+        del cav
+        torch.cuda.empty_cache()
+    m = c["parity_n"]
+    cpu, ref, robs = cpu_baseline_reduced(phys, m, c["steps"])
+    errors = {}
+    for st in ("f32", "f16", "bf16"):
+        cav = Cavity(m, m, stream=stream, storage=st, **phys)
+        cav.set_schedule(*scheds[st]).set_fields().step(c["steps"])
+        got, gobs = cav.fields(), cav.observables()
+        cav.close()
+        e = _field_err(got, ref)
+        e["Nu_max_rel"] = max(float(abs(gobs[k] - robs[k]) / abs(robs[k]))
+                              for k in ("Nu_f_hot", "Nu_s_hot", "Nu_f_cold", "Nu_s_cold"))
+        errors[st] = e
+    bpl = {"f32": 152, "f16": 76, "bf16": 76}
+    return {"mlups": rates, "lattice": "%dx%d" % (n, n), "steps": steps, "schedules": scheds,
+            "gpu_launches": launches,
+            "vs_plain_fp32_storage": {st: rates[st] / rates["f32"] for st in rates},
+            "roofline": {st: {"bound": "hbm", "achieved": bpl[st] * rates[st] / 1e3,
+                              "peak": peak, "unit": "GB/s",
+                              "frac": bpl[st] * rates[st] / 1e3 / peak,
+                              "bytes_per_lup": bpl[st]} for st in rates},
+            "errors_vs_oracle": {"run": "%dx%d, %d steps" % (m, m, c["steps"]),
+                                 "fields": errors, "tolerance": 1e-3},
+            "cpu_baseline": cpu, "clocks": clocks}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle, as it stands, on the host cores."""
     ws, rank, _ = dist_env()
@@ -277,11 +510,15 @@ def run_reference(args):
     value = m * m * args.steps / dt / 1e6
     sample = ("FP64 oracle on a %dx%d cavity with the same physics per step (bounded sample "
               "of the %dx%d workload)" % (m, m, args.n, args.n))
+    # the lattice this arm actually runs; MLUPS is a per-node rate, so it
+    # compares with the full-size line
+    config = dict(workload_config(m, args.storage), storage="f64",
+                  sample_of="%dx%d" % (args.n, args.n))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.n, args.storage),
+            "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -677,6 +914,14 @@ def main():
             torch.distributed.destroy_process_group()
         return
     cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline_oracle(n)
+    forms = None
+    if not args.no_forms and ws == 1:
+        del cav
+        torch.cuda.empty_cache()
+        gpu = None if args.no_clocks else local
+        forms = {"batched_256_cavities": form_batched(stream, value, peak, gpu),
+                 "adjoint_256": form_adjoint(stream, peak, gpu),
+                 "reduced_storage_8192": form_reduced(stream, value, peak, gpu)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
@@ -703,6 +948,7 @@ def main():
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "observables": {"Nu_f_hot": ob["Nu_f_hot"], "Nu_s_hot": ob["Nu_s_hot"],
                         "nonfinite": ob["nonfinite"], "step": ob["step"]},
+        "forms": forms,
     }
     if ws > 1:
         line["config"]["parallelism"] = "replicas x%d (independent cavities)" % ws

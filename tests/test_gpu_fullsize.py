@@ -130,14 +130,15 @@ def _c2_long_reference(n, steps):
     return _C2_LONG[key]
 
 
-@pytest.mark.parametrize("schedule", [(64, 2, 1), (128, 1, 2)])
-def test_c2_physics_1024_full_field_2500_steps(schedule):
-    """The throughput configuration's own physics at 1024 x 1024 from rest
-    for 2500 steps, full fields against the oracle: rel-L2 of u, T_f and
-    T_s within 1e-5 and the four wall Nusselt numbers within 1e-4, with one
+@pytest.mark.parametrize("n,steps,schedule", [(1024, 2500, (64, 2, 1)), (1024, 2500, (128, 1, 2)),
+                                               (512, 10_000, (64, 2, 1))])
+def test_c2_physics_full_field_long_run(n, steps, schedule):
+    """The throughput configuration's own physics from rest, full fields
+    against the oracle: rel-L2 of u, T_f and T_s within 1e-5 and the four
+    wall Nusselt numbers within 1e-4.  At 1024 x 1024 for 2500 steps with one
     node per thread (the default at this size) and with two nodes per thread
-    in 128 x 1 blocks (the 4096 x 4096 default)."""
-    n, steps = 1024, 2500
+    in 128 x 1 blocks (the 4096 x 4096 default); at 512 x 512 for the 10^4
+    steps the FP32 target is stated for."""
     phi, ref, ob_ref = _c2_long_reference(n, steps)
     cfg = dict(W.C2_THROUGHPUT, nx=n, ny=n)
     cav = cavity_for(cfg, storage="f32", phi=phi).set_schedule(*schedule)
@@ -150,4 +151,4 @@ def test_c2_physics_1024_full_field_2500_steps(schedule):
     for k in ("Nu_f_hot", "Nu_s_hot", "Nu_f_cold", "Nu_s_cold"):
         assert ob[k] == pytest.approx(ob_ref[k], rel=1e-4), (k, ob[k], ob_ref[k])
     assert ob["mass"] == pytest.approx(ob_ref["mass"], rel=1e-6)
-    assert ob["max_u"] > 1e-3  # the cavity convects
+    assert ob["max_u"] > 1e-4  # the flow has started (1024^2: max |u| 3.8e-4 after 2500 steps)

@@ -44,9 +44,13 @@ def run_pair(cfg, steps, storage, phi=None, bc=0, fields=None):
     return c, o
 
 
+# The periodic box has no walls to hold the buoyant flow back: with seed 4's
+# draw its flow accelerates past |u| = 0.2 and the method itself diverges
+# (the oracle as much as the CUDA path), which compares nothing; seed 24
+# keeps |u| below 0.01.
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("shape,bc,seed", [((8, 8), 0, 1), ((16, 16), 0, 2), ((13, 11), 0, 3),
-                                           ((9, 17), 1, 4), ((12, 10), 2, 5), ((5, 4), 0, 6)])
+                                           ((9, 17), 1, 24), ((12, 10), 2, 5), ((5, 4), 0, 6)])
 def test_brute_force_small(storage, shape, bc, seed):
     nx, ny = shape
     cfg = W.random_params(seed, nx, ny)
