@@ -249,6 +249,101 @@ int ltne_get_staging(const ltne_handle* h, int32_t* staged);
 size_t ltne_slab_scratch_bytes(const ltne_handle* h, int32_t nslabs);
 int ltne_step_slabs(ltne_handle* h, int32_t nslabs, int64_t n, void* scratch, size_t bytes);
 
+/* ------------------------------------------------------------------------
+ * One row slab of the cavity per process (no counterpart in the paper,
+ * which has no parallel code; its Sec. 1 notes the method's low
+ * communication-to-computation ratio).  The lattice is cut into nslabs
+ * slabs of consecutive rows; each process (typically one per GPU) creates a
+ * slab handle for its own slab and, after every step, swaps the values that
+ * stream across each cut with its neighbours through its own communicator
+ * (NCCL, MPI, host-staged sockets ...).  With pull streaming a row reads
+ * from the row below only the populations that stream up (e_y = +1: f_2,
+ * f_5, f_6 and g_2 of both temperature lattices) and from the row above only
+ * those that stream down (e_y = -1: f_4, f_7, f_8, g_4 of both): one message
+ * of 5 x nx values per cut and direction and step.  Walls need no exchange
+ * (the side walls lie in every slab, the bottom and top walls in the end
+ * slabs).  The slabs' computed rows are the same bits as the undivided
+ * lattice run with one node per thread (ltne_set_schedule(h, 64, 2, 1)).
+ * Restrictions: cavity walls, FP32 or FP64 storage, no local h_v, at least 2
+ * rows per slab; an Ergun permeability with a porosity field needs p->d_p > 0
+ * (the diameter belongs to the whole field: ltne_ergun_diameter).
+ * Sequence per process:
+ *   ltne_create_slab -> ltne_workspace_bytes / ltne_bind_workspace ->
+ *   ltne_set_fields (arrays of the LOCAL lattice: rows y0 - halo_lo ..
+ *   y0 + rows - 1 + halo_hi of the cavity, nx per row; the halo rows take
+ *   the neighbours' initial values) -> per step: ltne_step_slab ->
+ *   exchange (send_lo -> the slab below's recv_hi, send_hi -> the slab
+ *   above's recv_lo) -> ltne_halo_unpack.
+ * ltne_step, ltne_observables, the adjoint, staging and two-node schedules
+ * return LTNE_ERR_INVALID_ARG on a slab handle; ltne_get_fields returns the
+ * local lattice (its halo rows hold no computed values); checkpoints work
+ * per slab.
+ * ---------------------------------------------------------------------- */
+
+/* Slab `index` of `nslabs` of a cavity of ny rows: first row *y0, *rows
+   rows (ny / nslabs, the first ny % nslabs slabs one more), and whether it
+   has a halo row below / above (a neighbouring slab).  Any output pointer
+   may be NULL.  INVALID_ARG unless 0 <= index < nslabs and ny / nslabs >= 2. */
+int ltne_slab_rows(int32_t ny, int32_t nslabs, int32_t index, int32_t* y0, int32_t* rows,
+                   int32_t* halo_lo, int32_t* halo_hi);
+
+/* Handle for slab `index` of `nslabs` of the cavity *p (p->nx, p->ny and
+   every other field describe the WHOLE cavity: the lattice constants,
+   L = ny - 1 included, are the cavity's).  Errors as ltne_create, plus
+   INVALID_ARG for the restrictions above. */
+int ltne_create_slab(const ltne_params* p, int32_t nslabs, int32_t index, void* cuda_stream,
+                     ltne_handle** out);
+
+/* Device addresses of the four message buffers inside the bound workspace
+   (NULL on a side without a neighbour) and their common size in bytes
+   (5 x nx values of the storage type).  send_lo / send_hi: the values this
+   slab gives the slab below / above, written by ltne_step_slab and
+   ltne_halo_pack; recv_lo / recv_hi: where the caller puts what the slab
+   below / above sent, read by ltne_halo_unpack.  The buffers hold, in this
+   order, plane by plane (nx values each): below, f_4 f_7 f_8 g_f4 g_s4;
+   above, f_2 f_5 f_6 g_f2 g_s2. */
+int ltne_halo_buffers(ltne_handle* h, void** send_lo, void** send_hi, void** recv_lo,
+                      void** recv_hi, size_t* bytes);
+
+/* One time step of the slab's rows (the halo rows are read, not updated),
+   then ltne_halo_pack.  write_macros = 1 also stores the macroscopic fields
+   (needed before ltne_slab_accumulators or ltne_get_fields); 0 skips them.
+   Asynchronous on the handle's stream: the send buffers are ready when the
+   stream reaches this point. */
+int ltne_step_slab(ltne_handle* h, int32_t write_macros);
+
+/* Copy the current state's outgoing values into send_lo / send_hi (e.g.
+   to fill the neighbours' halos right after ltne_set_fields or
+   ltne_set_state), and the received values from recv_lo / recv_hi into the
+   halo rows.  Asynchronous on the handle's stream. */
+int ltne_halo_pack(ltne_handle* h);
+int ltne_halo_unpack(ltne_handle* h);
+
+/* The slab's share of the observables: LTNE_NACC FP64 accumulators of its
+   computed rows (the wall-flux integrals take the trapezoid's half weight
+   only at the cavity's bottom and top rows), as left by the last step with
+   write_macros = 1.  Updates the slab's residual snapshot.  Synchronises. */
+#define LTNE_NACC 18
+int ltne_slab_accumulators(ltne_handle* h, double* acc, int32_t nacc);
+
+/* acc <- acc combined with other (sums; the two maxima take the larger).
+   Combining the slabs' vectors in slab order on every process gives every
+   process the same bits. */
+int ltne_accumulators_combine(double* acc, const double* other, int32_t nacc);
+
+/* Observables of the whole cavity *p from its combined accumulators, after
+   `step` steps; have_prev = 0 on the first reduction of a run (residual
+   NaN), 1 after.  Returns LTNE_ERR_NONFINITE (with *out filled) if any
+   node was non-finite.  Host only. */
+int ltne_observables_from_accumulators(const ltne_params* p, int64_t step, int32_t have_prev,
+                                       const double* acc, int32_t nacc, ltne_obs* out);
+
+/* The Ergun particle diameter that makes the mean of K / L^2 over the n
+   porosities equal Da (Eq. 7), with the arithmetic ltne_set_fields uses
+   for d_p <= 0 (so a slab given it matches the undivided lattice bit for
+   bit).  Host only. */
+int ltne_ergun_diameter(const double* porosity, int64_t n, double L, double Da, double* d);
+
 /* Self-check of the bounded wait of the staged step (no counterpart in the
    paper): one GPU thread waits, with at most `spins` polls, on an mbarrier
    phase that can never complete; *gave_up = 1 when the wait returned

@@ -774,14 +774,15 @@ int ltne_get_adjoint_schedule(const ltne_handle* h, int32_t* mode) {
 }
 
 size_t ltne_adjoint_workspace_bytes(const ltne_handle* h, int64_t n_steps, int32_t segment) {
-  if (!h || n_steps < 1 || segment < 1) return 0;
+  if (!h || n_steps < 1 || segment < 1 || h->slab) return 0;
   return adj_layout(h, n_steps, segment).total;
 }
 
 int ltne_adjoint(ltne_handle* h, const double* porosity, const double* rho, const double* T_f,
                  const double* T_s, int64_t n_steps, int32_t segment, void* adj_workspace,
                  size_t bytes, void* dJ_dphi, double* J, double* dJ_dH) {
-  if (!h || !porosity || !J || !dJ_dH || n_steps < 1 || segment < 1 || !adj_workspace)
+  if (!h || !porosity || !J || !dJ_dH || n_steps < 1 || segment < 1 || !adj_workspace ||
+      h->slab)
     return LTNE_ERR_INVALID_ARG;
   if (!h->ws) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;

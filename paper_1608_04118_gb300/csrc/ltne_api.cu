@@ -237,6 +237,21 @@ int download_field(ltne_handle* h, const char* dev, Drain drain) {
 
 namespace ltne {
 
+double ergun_mean(const double* porosity, int64_t n) {
+  double part[kHostChunks] = {0};
+  host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
+    double s = 0.0;
+    for (int64_t k = lo; k < hi; ++k) {
+      const double ph = porosity[k];
+      s += ph * ph * ph / ((1 - ph) * (1 - ph));
+    }
+    part[c] = s;
+  });
+  double acc = 0.0;
+  for (int c = 0; c < kHostChunks; ++c) acc += part[c];
+  return acc / (double)n;
+}
+
 // Lattice constants from the problem statement.  Returns a status code.
 int derive_params(const ltne_params& p, const double* porosity, NodeParams<double>& P,
                   DerivedInfo& info) {
@@ -297,17 +312,7 @@ int derive_params(const ltne_params& p, const double* porosity, NodeParams<doubl
       double acc = 0.0;
       const int64_t n = (int64_t)p.nx * p.ny;
       if (porosity) {
-        double part[kHostChunks] = {0};
-        host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
-          double s = 0.0;
-          for (int64_t k = lo; k < hi; ++k) {
-            const double ph = porosity[k];
-            s += ph * ph * ph / ((1 - ph) * (1 - ph));
-          }
-          part[c] = s;
-        });
-        for (int c = 0; c < kHostChunks; ++c) acc += part[c];
-        acc /= (double)n;
+        acc = ergun_mean(porosity, n);
       } else {
         const double ph = p.porosity;
         acc = ph * ph * ph / ((1 - ph) * (1 - ph));
@@ -426,7 +431,9 @@ namespace {
 
 int derive(ltne_handle* h, const double* porosity) {
   DerivedInfo info;
-  const int rc = derive_params(h->p, porosity, h->P, info);
+  ltne_params pg = h->p;
+  if (h->slab) pg.ny = h->gny;  // a slab takes the lattice constants of the whole cavity
+  const int rc = derive_params(pg, h->slab ? nullptr : porosity, h->P, info);
   if (rc == LTNE_OK) {
     h->L = info.L;
     h->nu_f = info.nu_f;
@@ -465,6 +472,10 @@ void layout(ltne_handle* h) {
     h->off_um[b] = off;
     if (p.hv_local) off = align_up(off + (size_t)h->plane * h->ec, A);
   }
+  for (int k = 0; k < 4; ++k) {  // a slab's halo messages: 5 x nx values each
+    h->off_halo[k] = off;
+    if (h->slab) off = align_up(off + 5 * (size_t)p.nx * h->es, A);
+  }
   h->ws_bytes = off;
   h->enc_scale = p.storage == LTNE_F16DEV ? 1024.0f : 1.0f;  // FP16 deviations x 2^10
 }
@@ -477,7 +488,8 @@ LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
   a.mac = h->ws + h->off_mac;
   a.nx = h->p.nx;
   a.ny = h->p.ny;
-  a.bc = h->p.bc;
+  a.bc = h->slab ? BC_SLAB : h->p.bc;
+  a.slab_walls = h->slab ? ((h->slo ? 0 : SLAB_LO_WALL) | (h->shi ? 0 : SLAB_HI_WALL)) : 0;
   a.write_macros = write_macros;
   a.pitch = h->pitch;
   a.plane = h->plane;
@@ -653,6 +665,18 @@ int reduce_launch(ltne_handle* h) {
   a.update_prev = 1;
   a.blocks = h->red_blocks;
   a.is_double = h->ec == 8;
+  if (h->slab) {
+    // the computed rows only, with the trapezoid's half weight at a row
+    // that is a wall of the whole cavity
+    const size_t skip = (size_t)h->slo * h->pitch * h->ec;
+    a.mac = static_cast<const char*>(a.mac) + skip;
+    if (a.phi) a.phi = static_cast<const char*>(a.phi) + skip;
+    a.prev = static_cast<char*>(a.prev) + skip;
+    a.ny = h->srows;
+    a.blocks = reduce_blocks(p.nx, h->srows);
+    a.wall_lo = h->slo ? 0 : 1;
+    a.wall_hi = h->shi ? 0 : 1;
+  }
   return fail_cuda(launch_reduce(a, h->stream));
 }
 
@@ -709,7 +733,7 @@ std::vector<SlabGeom> slab_layout(const ltne_handle* h, int nslabs) {
 }
 
 bool slabs_supported(const ltne_handle* h, int nslabs) {
-  return h && nslabs >= 1 && h->p.bc == LTNE_BC_CAVITY && !h->p.hv_local &&
+  return h && !h->slab && nslabs >= 1 && h->p.bc == LTNE_BC_CAVITY && !h->p.hv_local &&
          (h->p.storage == LTNE_F32 || h->p.storage == LTNE_F64) && h->p.ny / nslabs >= 2;
 }
 
@@ -821,7 +845,7 @@ int ltne_set_fields(ltne_handle* h, const double* porosity, const double* rho, c
 }
 
 int ltne_step(ltne_handle* h, int64_t n) {
-  if (!h || n < 0) return LTNE_ERR_INVALID_ARG;
+  if (!h || n < 0 || h->slab) return LTNE_ERR_INVALID_ARG;
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
   if (n == 0) return LTNE_OK;
   int64_t plain = n - 1;  // the last step also writes the macroscopic fields
@@ -855,7 +879,7 @@ int ltne_step(ltne_handle* h, int64_t n) {
 }
 
 int ltne_observables(ltne_handle* h, ltne_obs* out) {
-  if (!h || !out) return LTNE_ERR_INVALID_ARG;
+  if (!h || !out || h->slab) return LTNE_ERR_INVALID_ARG;
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;
   cudaError_t e = cudaSuccess;
@@ -1018,7 +1042,8 @@ int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
   if (block_x < 32 || block_x > 256 || block_x % 32 != 0 || block_y < 1 || threads > 256)
     return LTNE_ERR_INVALID_ARG;
   if (nodes_per_thread != 1 && nodes_per_thread != 2) return LTNE_ERR_INVALID_ARG;
-  if (nodes_per_thread == 2 && (h->p.storage == LTNE_F64 || threads > kPairBlockThreads))
+  if (nodes_per_thread == 2 &&
+      (h->p.storage == LTNE_F64 || threads > kPairBlockThreads || h->slab))
     return LTNE_ERR_INVALID_ARG;
   h->shape.bx = block_x;
   h->shape.by = block_y;
@@ -1103,8 +1128,140 @@ int ltne_step_slabs(ltne_handle* h, int32_t nslabs, int64_t n, void* scratch, si
   return LTNE_OK;
 }
 
+// ---- a row slab per process ------------------------------------------------
+
+int ltne_slab_rows(int32_t ny, int32_t nslabs, int32_t index, int32_t* y0, int32_t* rows,
+                   int32_t* halo_lo, int32_t* halo_hi) {
+  if (ny < 4 || nslabs < 1 || index < 0 || index >= nslabs || ny / nslabs < 2)
+    return LTNE_ERR_INVALID_ARG;
+  const int base = ny / nslabs, extra = ny % nslabs;
+  if (y0) *y0 = index * base + std::min(index, extra);
+  if (rows) *rows = base + (index < extra ? 1 : 0);
+  if (halo_lo) *halo_lo = index > 0 ? 1 : 0;
+  if (halo_hi) *halo_hi = index < nslabs - 1 ? 1 : 0;
+  return LTNE_OK;
+}
+
+int ltne_create_slab(const ltne_params* p, int32_t nslabs, int32_t index, void* cuda_stream,
+                     ltne_handle** out) {
+  if (!p || !out) return LTNE_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = validate_params(*p);
+  if (rc != LTNE_OK) return rc;
+  if (p->bc != LTNE_BC_CAVITY || p->hv_local ||
+      (p->storage != LTNE_F32 && p->storage != LTNE_F64))
+    return LTNE_ERR_INVALID_ARG;
+  // the Ergun diameter belongs to the whole porosity field, which no slab sees
+  if (p->permeability == LTNE_K_ERGUN && p->porosity_field && !(p->d_p > 0))
+    return LTNE_ERR_INVALID_ARG;
+  int32_t y0 = 0, rows = 0, lo = 0, hi = 0;
+  rc = ltne_slab_rows(p->ny, nslabs, index, &y0, &rows, &lo, &hi);
+  if (rc != LTNE_OK) return rc;
+  ltne_handle* h = new ltne_handle();
+  h->p = *p;
+  h->slab = 1;
+  h->nslabs = nslabs;
+  h->slab_index = index;
+  h->gny = p->ny;
+  h->g0 = y0;
+  h->srows = rows;
+  h->slo = lo;
+  h->shi = hi;
+  h->p.ny = rows + lo + hi;  // the local lattice
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  rc = derive(h, nullptr);
+  if (rc != LTNE_OK) {
+    delete h;
+    return rc;
+  }
+  layout(h);  // one node per thread, 64 x 2 blocks (the slab kernel's form)
+  *out = h;
+  return LTNE_OK;
+}
+
+int ltne_halo_buffers(ltne_handle* h, void** send_lo, void** send_hi, void** recv_lo,
+                      void** recv_hi, size_t* bytes) {
+  if (!h || !h->slab) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws) return LTNE_ERR_STATE;
+  void* ptr[4];
+  for (int k = 0; k < 4; ++k) {
+    const bool has = (k & 1) ? h->shi : h->slo;
+    ptr[k] = has ? h->ws + h->off_halo[k] : nullptr;
+  }
+  if (send_lo) *send_lo = ptr[0];
+  if (send_hi) *send_hi = ptr[1];
+  if (recv_lo) *recv_lo = ptr[2];
+  if (recv_hi) *recv_hi = ptr[3];
+  if (bytes) *bytes = 5 * (size_t)h->p.nx * h->es;
+  return LTNE_OK;
+}
+
+int ltne_halo_pack(ltne_handle* h) {
+  if (!h || !h->slab) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  return fail_cuda(launch_halo_pack(h->ws + h->off_pop[h->cur], h->pitch, h->plane, h->p.nx,
+                                    h->slo, h->slo + h->srows - 1, h->es,
+                                    h->slo ? h->ws + h->off_halo[0] : nullptr,
+                                    h->shi ? h->ws + h->off_halo[1] : nullptr, h->stream));
+}
+
+int ltne_halo_unpack(ltne_handle* h) {
+  if (!h || !h->slab) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  return fail_cuda(launch_halo_unpack(h->ws + h->off_pop[h->cur], h->pitch, h->plane, h->p.nx,
+                                      0, h->p.ny - 1, h->es,
+                                      h->slo ? h->ws + h->off_halo[2] : nullptr,
+                                      h->shi ? h->ws + h->off_halo[3] : nullptr, h->stream));
+}
+
+int ltne_step_slab(ltne_handle* h, int32_t write_macros) {
+  if (!h || !h->slab || (write_macros != 0 && write_macros != 1)) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  const cudaError_t e = launch_step(h, h->cur, write_macros, h->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  h->cur ^= 1;
+  ++h->step;
+  ++h->launches;
+  return ltne_halo_pack(h);
+}
+
+int ltne_slab_accumulators(ltne_handle* h, double* acc, int32_t nacc) {
+  if (!h || !h->slab || !acc || nacc != NACC) return LTNE_ERR_INVALID_ARG;
+  if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  return reduce_handle(h, acc);
+}
+
+int ltne_accumulators_combine(double* acc, const double* other, int32_t nacc) {
+  if (!acc || !other || nacc != NACC) return LTNE_ERR_INVALID_ARG;
+  for (int k = 0; k < NACC; ++k)
+    acc[k] = (k == A_MAXU || k == A_MAXDT) ? fmax(acc[k], other[k]) : acc[k] + other[k];
+  return LTNE_OK;
+}
+
+int ltne_observables_from_accumulators(const ltne_params* p, int64_t step, int32_t have_prev,
+                                       const double* acc, int32_t nacc, ltne_obs* out) {
+  if (!p || !acc || !out || nacc != NACC) return LTNE_ERR_INVALID_ARG;
+  int rc = validate_params(*p);
+  if (rc != LTNE_OK) return rc;
+  NodeParams<double> P;
+  DerivedInfo info;
+  ltne_params q = *p;
+  if (q.permeability == LTNE_K_ERGUN && q.porosity_field && !(q.d_p > 0)) q.d_p = 1.0;
+  rc = derive_params(q, nullptr, P, info);  // L and alpha_f (no diameter is needed)
+  if (rc != LTNE_OK) return rc;
+  return finish_observables(*p, info, step, have_prev != 0, acc, out);
+}
+
+int ltne_ergun_diameter(const double* porosity, int64_t n, double L, double Da, double* d) {
+  if (!porosity || n < 1 || !d || !(L > 0) || !(Da > 0)) return LTNE_ERR_INVALID_ARG;
+  for (int64_t k = 0; k < n; ++k)
+    if (!in_open(porosity[k], 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
+  *d = L * sqrt(150.0 * Da / ergun_mean(porosity, n));
+  return LTNE_OK;
+}
+
 int ltne_set_staging(ltne_handle* h, int32_t staged) {
-  if (!h || (staged != 0 && staged != 1)) return LTNE_ERR_INVALID_ARG;
+  if (!h || (staged != 0 && staged != 1) || (staged && h->slab)) return LTNE_ERR_INVALID_ARG;
   if (staged && (h->p.storage == LTNE_F64 || h->p.bc != LTNE_BC_CAVITY))
     return LTNE_ERR_INVALID_ARG;
   h->shape.tma = staged;

@@ -36,6 +36,15 @@ struct ltne_handle {
   // two pinned host buffers that stage whole fields in and out (allocated
   // at the first set_fields / get_fields, freed by ltne_destroy)
   char* pin[2] = {nullptr, nullptr};
+  // Row slab of a cavity advanced by one process (ltne_create_slab): the
+  // local lattice is the slab's computed rows with a halo row towards each
+  // neighbouring slab; p.ny counts the local rows, gny the cavity's.
+  int slab = 0;
+  int nslabs = 1, slab_index = 0;
+  int gny = 0;             // rows of the whole cavity
+  int g0 = 0, srows = 0;   // first global row computed here, rows computed
+  int slo = 0, shi = 0;    // halo row below / above (0 or 1)
+  size_t off_halo[4] = {0, 0, 0, 0};  // send below, send above, receive below, above
   // pinned landing place of the observables' accumulators and the device
   // error word (one asynchronous read-back per ltne_observables call)
   double* pin_obs = nullptr;

@@ -114,9 +114,30 @@ struct ReduceArgs {
   int update_prev;
   int blocks;
   int is_double;     // macro planes hold doubles (else floats)
+  // 1: the first / last reduced row is a wall row of the cavity (half
+  // trapezoid weight in the wall-flux integrals); 0 for the inner edge of a
+  // row slab
+  int wall_lo = 1, wall_hi = 1;
 };
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
+
+// Halo rows of a row slab (ltne_slab.cu).  Pack: the populations of the
+// slab's first computed row that stream down (e_y = -1: f_4, f_7, f_8,
+// g_f4, g_s4) into send_lo, those of its last computed row that stream up
+// (e_y = +1: f_2, f_5, f_6, g_f2, g_s2) into send_hi, 5 x nx values each.
+// Unpack: recv_lo into the same five e_y = +1 planes of the halo row below,
+// recv_hi into the e_y = -1 planes of the halo row above.  A null buffer
+// skips its side.  Element size es (4 or 8 bytes).
+cudaError_t launch_halo_pack(const void* pops, int64_t pitch, int64_t plane, int nx, int row_lo,
+                             int row_hi, size_t es, void* send_lo, void* send_hi,
+                             cudaStream_t st);
+cudaError_t launch_halo_unpack(void* pops, int64_t pitch, int64_t plane, int nx, int halo_lo,
+                               int halo_hi, size_t es, const void* recv_lo, const void* recv_hi,
+                               cudaStream_t st);
+// Mean of phi^3 / (1 - phi)^2 over n porosities, summed in a fixed order
+// (the Ergun particle diameter follows from it).
+double ergun_mean(const double* porosity, int64_t n);
 
 // Host-side parameter mapping and observables (ltne_api.cu), shared with
 // the batched form.

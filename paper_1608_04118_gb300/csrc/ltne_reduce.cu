@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
       for (int r = 0; r < RU; ++r) {
         const int y = yg + r;
         if (y >= y1) break;
-        const C wy = (y == 0 || y == a.ny - 1) ? C(0.5) : C(1);
+        const C wy = ((y == 0 && a.wall_lo) || (y == a.ny - 1 && a.wall_hi)) ? C(0.5) : C(1);
         acc[A_NUF_H] += whot * wy * Tf[r];
         acc[A_NUS_H] += whot * wy * Ts[r];
         acc[A_NUF_C] += wcold * wy * Tf[r];

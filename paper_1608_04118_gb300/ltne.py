@@ -106,6 +106,19 @@ SIGNATURES = {
                                _dp, _dp]),
     "ltne_destroy": (None, [_vp]),
     "ltne_error_string": (C.c_char_p, [C.c_int]),
+    "ltne_slab_rows": (C.c_int, [C.c_int32, C.c_int32, C.c_int32] + [C.POINTER(C.c_int32)] * 4),
+    "ltne_create_slab": (C.c_int, [C.POINTER(ltne_params), C.c_int32, C.c_int32, _vp,
+                                   C.POINTER(_vp)]),
+    "ltne_halo_buffers": (C.c_int, [_vp] + [C.POINTER(_vp)] * 4 + [C.POINTER(C.c_size_t)]),
+    "ltne_step_slab": (C.c_int, [_vp, C.c_int32]),
+    "ltne_halo_pack": (C.c_int, [_vp]),
+    "ltne_halo_unpack": (C.c_int, [_vp]),
+    "ltne_slab_accumulators": (C.c_int, [_vp, _dp, C.c_int32]),
+    "ltne_accumulators_combine": (C.c_int, [_dp, _dp, C.c_int32]),
+    "ltne_observables_from_accumulators": (C.c_int, [C.POINTER(ltne_params), C.c_int64,
+                                                     C.c_int32, _dp, C.c_int32,
+                                                     C.POINTER(ltne_obs)]),
+    "ltne_ergun_diameter": (C.c_int, [_dp, C.c_int64, C.c_double, C.c_double, _dp]),
     "ltne_batch_create": (C.c_int, [C.POINTER(ltne_params), C.c_int32, _vp, C.POINTER(_vp)]),
     "ltne_batch_workspace_bytes": (C.c_size_t, [_vp]),
     "ltne_batch_nodes": (C.c_int64, [_vp]),
@@ -307,6 +320,80 @@ def ltne_error_string(code: int) -> str:
     return _lib().ltne_error_string(int(code)).decode()
 
 
+LTNE_NACC = 18
+
+
+def ltne_slab_rows(ny, nslabs, index):
+    """(y0, rows, halo_lo, halo_hi) of slab `index` of `nslabs`."""
+    v = [C.c_int32() for _ in range(4)]
+    _check(_lib().ltne_slab_rows(int(ny), int(nslabs), int(index), *[C.byref(x) for x in v]),
+           "ltne_slab_rows")
+    return tuple(x.value for x in v)
+
+
+def ltne_create_slab(params: ltne_params, nslabs, index, stream=None):
+    h = _vp()
+    s = _vp(int(stream) if stream is not None else 0)
+    _check(_lib().ltne_create_slab(C.byref(params), int(nslabs), int(index), s, C.byref(h)),
+           "ltne_create_slab")
+    return h
+
+
+def ltne_halo_buffers(h):
+    """(send_lo, send_hi, recv_lo, recv_hi, bytes): device addresses (None
+    on a side without a neighbour) and the message size."""
+    v = [_vp() for _ in range(4)]
+    nb = C.c_size_t()
+    _check(_lib().ltne_halo_buffers(h, *[C.byref(x) for x in v], C.byref(nb)),
+           "ltne_halo_buffers")
+    return tuple(x.value for x in v) + (nb.value,)
+
+
+def ltne_step_slab(h, write_macros):
+    _check(_lib().ltne_step_slab(h, int(write_macros)), "ltne_step_slab")
+
+
+def ltne_halo_pack(h):
+    _check(_lib().ltne_halo_pack(h), "ltne_halo_pack")
+
+
+def ltne_halo_unpack(h):
+    _check(_lib().ltne_halo_unpack(h), "ltne_halo_unpack")
+
+
+def ltne_slab_accumulators(h) -> np.ndarray:
+    acc = np.zeros(LTNE_NACC)
+    _check(_lib().ltne_slab_accumulators(h, _ptr(acc), LTNE_NACC), "ltne_slab_accumulators")
+    return acc
+
+
+def ltne_accumulators_combine(acc, other) -> np.ndarray:
+    a = np.array(acc, dtype=np.float64)
+    b = _f64(other, LTNE_NACC)
+    _check(_lib().ltne_accumulators_combine(_ptr(a), _ptr(b), LTNE_NACC),
+           "ltne_accumulators_combine")
+    return a
+
+
+def ltne_observables_from_accumulators(params: ltne_params, step, have_prev, acc,
+                                       allow_nonfinite=False) -> dict:
+    a = _f64(acc, LTNE_NACC)
+    o = ltne_obs()
+    rc = _lib().ltne_observables_from_accumulators(C.byref(params), int(step), int(have_prev),
+                                                   _ptr(a), LTNE_NACC, C.byref(o))
+    if not (rc == LTNE_OK or (allow_nonfinite and rc == LTNE_ERR_NONFINITE)):
+        raise LtneError(rc, "ltne_observables_from_accumulators")
+    return o.as_dict()
+
+
+def ltne_ergun_diameter(porosity, L, Da) -> float:
+    a = np.ascontiguousarray(np.asarray(porosity, dtype=np.float64)).reshape(-1)
+    d = C.c_double()
+    _check(_lib().ltne_ergun_diameter(_ptr(a), a.size, float(L), float(Da), C.byref(d)),
+           "ltne_ergun_diameter")
+    return d.value
+
+
 # ---- convenience object ----------------------------------------------------
 
 class Cavity:
@@ -426,6 +513,97 @@ class Cavity:
         J, dH = ltne_adjoint(self.h, self.nodes, porosity, n_steps, segment, ws.data_ptr(), nbytes,
                              g.data_ptr(), rho=rho, T_f=T_f, T_s=T_s)
         return J, g, dH
+
+    def close(self):
+        if getattr(self, "h", None):
+            ltne_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SlabCavity:
+    """One row slab of a cavity, advanced by this process, on the current
+    CUDA device.  ``SlabCavity(nx, ny, nslabs, index, **params)``: nx, ny and
+    the parameters describe the whole cavity.  The halo exchange between
+    steps is the caller's (``paper_1608_04118_gb300.slabs`` moves it with
+    torch.distributed)."""
+
+    def __init__(self, nx, ny, nslabs, index, stream=None, device=None, **params):
+        import torch
+
+        self.nx, self.ny_global = int(nx), int(ny)
+        self.nslabs, self.index = int(nslabs), int(index)
+        self.params = ltne_default_params(nx, ny, **params)
+        self.y0, self.rows, self.halo_lo, self.halo_hi = ltne_slab_rows(ny, nslabs, index)
+        self.ny = self.rows + self.halo_lo + self.halo_hi  # local rows
+        dev = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        self.h = ltne_create_slab(self.params, nslabs, index, stream.cuda_stream)
+        nbytes = ltne_workspace_bytes(self.h)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        ltne_bind_workspace(self.h, self.workspace.data_ptr(), nbytes)
+        self.buffers = ltne_halo_buffers(self.h)
+        self.have_prev = False
+
+    @property
+    def local_rows(self):
+        """Rows [a, b) of the cavity that the local lattice covers (halos
+        included)."""
+        return self.y0 - self.halo_lo, self.y0 + self.rows + self.halo_hi
+
+    def local(self, field):
+        """The local lattice's part of a whole-cavity field (ny x nx)."""
+        if field is None:
+            return None
+        a, b = self.local_rows
+        return np.asarray(field, dtype=np.float64).reshape(self.ny_global, self.nx)[a:b]
+
+    def set_fields(self, porosity=None, rho=None, ux=None, uy=None, T_f=None, T_s=None):
+        """Initial fields given for the WHOLE cavity (any may be None)."""
+        ltne_set_fields(self.h, self.nx * self.ny, *[self.local(f) for f in
+                                                      (porosity, rho, ux, uy, T_f, T_s)])
+        self.have_prev = False
+        return self
+
+    def step(self, write_macros):
+        ltne_step_slab(self.h, write_macros)
+        return self
+
+    def pack(self):
+        ltne_halo_pack(self.h)
+        return self
+
+    def unpack(self):
+        ltne_halo_unpack(self.h)
+        return self
+
+    def accumulators(self):
+        return ltne_slab_accumulators(self.h)
+
+    def fields(self):
+        """Macroscopic fields of the slab's computed rows (rows x nx)."""
+        f = ltne_get_fields(self.h, self.nx, self.ny)
+        a = self.halo_lo
+        return {k: v[a:a + self.rows] for k, v in f.items()}
+
+    def get_state(self):
+        return ltne_get_state(self.h)
+
+    def set_state(self, blob):
+        ltne_set_state(self.h, blob)
+        return self
+
+    @property
+    def launches(self):
+        return ltne_launch_count(self.h)
 
     def close(self):
         if getattr(self, "h", None):
