@@ -488,7 +488,7 @@ int run_adjoint(ltne_handle* h, const double* porosity, const double* rho, const
   if (rc != LTNE_OK) return rc;
   const NodeParams<C> P = cast_params<C>(h->P);
   const C* phi = reinterpret_cast<const C*>(h->ws + h->off_phi);
-  C* mac = reinterpret_cast<C*>(h->ws + h->off_mac);
+  C* mac = reinterpret_cast<C*>(mac_cur(h));  // set 0 after set_fields, no snapshot
   // 64 x 2 blocks: measured against 128 x 2, 128 x 1, 256 x 1, 32 x 4,
   // 64 x 1 and 32 x 2 (the recompute shares the SMs with the reverse sweep;
   // 256^2: 5,530 against 5,456 MLUPS with 128 x 2, 1024^2: 9,548 against

@@ -457,15 +457,25 @@ void layout(ltne_handle* h) {
   }
   h->off_phi = off;
   if (p.porosity_field) off = align_up(off + (size_t)h->plane * h->ec, A);
-  h->off_mac = off;
-  off = align_up(off + 5 * (size_t)h->plane * h->ec, A);
-  h->off_prev = off;
-  off = align_up(off + 4 * (size_t)h->plane * h->ec, A);
+  for (int b = 0; b < 2; ++b) {  // the current fields and the residual snapshot
+    h->off_mac[b] = off;
+    off = align_up(off + 5 * (size_t)h->plane * h->ec, A);
+  }
   h->red_blocks = reduce_blocks(p.nx, p.ny);
   h->off_part = off;
   off = align_up(off + (size_t)h->red_blocks * NACC * sizeof(double), A);
   h->off_out = off;
   off = align_up(off + NACC * sizeof(double), A);
+  // block partials of the observables fused into the last step of a call:
+  // room for the grids of the default launch shapes (64 x 2 one node per
+  // thread; two nodes per thread in 128 x 1 or 32 x 4), and for the first
+  // level of their combination
+  h->fpart_cap = (int64_t)((p.nx + 63) / 64) * ((p.ny + 1) / 2);
+  h->off_fpart = off;
+  off = align_up(off + (size_t)h->fpart_cap * NACC * sizeof(double), A);
+  h->off_fpart2 = off;
+  off = align_up(off + (size_t)((h->fpart_cap + kObsChunk - 1) / kObsChunk) * NACC *
+                           sizeof(double), A);
   h->off_tick = off;  // two uint32 step counters for the stochastic rounding, then
   off = align_up(off + 3 * sizeof(uint32_t), A);  // the device error word
   for (int b = 0; b < 2; ++b) {  // |u| of the previous state per buffer (Eq. 52)
@@ -485,7 +495,7 @@ LatticeArgs lattice_args(const ltne_handle* h, int src_buf, int write_macros) {
   a.src = h->ws + h->off_pop[src_buf];
   a.dst = h->ws + h->off_pop[src_buf ^ 1];
   a.phi = h->p.porosity_field ? h->ws + h->off_phi : nullptr;
-  a.mac = h->ws + h->off_mac;
+  a.mac = mac_cur(h);  // a launch that writes the fields calls begin_macro_write first
   a.nx = h->p.nx;
   a.ny = h->p.ny;
   a.bc = h->slab ? BC_SLAB : h->p.bc;
@@ -515,6 +525,20 @@ cudaError_t launch_step(ltne_handle* h, int src_buf, int write_macros, cudaStrea
     case LTNE_F16DEV: return launch_step_f16(a, h->P, h->shape, st);
     default: return launch_step_bf16(a, h->P, h->shape, st);
   }
+}
+
+// Point the current macro set at the one the next write of the fields
+// goes to (never the residual snapshot) and forget the fused partials.
+void begin_macro_write(ltne_handle* h) {
+  h->mcur = mac_next(h);
+  h->fused_valid = false;
+}
+
+// Blocks of the step grid for the handle's launch shape.
+int64_t step_blocks(const ltne_handle* h) {
+  const int64_t cols = h->shape.pair ? (h->p.nx + 1) / 2 : h->p.nx;
+  return ((cols + h->shape.bx - 1) / h->shape.bx) * (((int64_t)h->p.ny + h->shape.by - 1) /
+                                                      h->shape.by);
 }
 
 void drop_graphs(ltne_handle* h) {
@@ -618,9 +642,12 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
       return true;
     });
   };
+  h->mcur = 0;  // the fields go to macro set 0; no residual snapshot yet
+  h->msnap = -1;
+  h->fused_valid = false;
   for (int k = 0; k < 5; ++k) {
     if (!src[k]) continue;
-    rc = stage(src[k], defaults[k], refs[k], h->ws + h->off_mac + (size_t)k * h->plane * h->ec);
+    rc = stage(src[k], defaults[k], refs[k], mac_cur(h) + (size_t)k * h->plane * h->ec);
     if (rc != LTNE_OK) return rc;
   }
   if (porosity) {
@@ -649,9 +676,11 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
 int reduce_launch(ltne_handle* h) {
   const ltne_params& p = h->p;
   ReduceArgs a;
-  a.mac = h->ws + h->off_mac;
+  a.mac = mac_cur(h);
   a.phi = p.porosity_field ? h->ws + h->off_phi : nullptr;
-  a.prev = h->ws + h->off_prev;
+  // the snapshot's u_x, u_y, T_f, T_s planes (the current ones when there is
+  // no snapshot or the fields have not changed since it: differences 0)
+  a.prev = h->ws + h->off_mac[h->msnap >= 0 ? h->msnap : h->mcur] + (size_t)h->plane * h->ec;
   a.partials = reinterpret_cast<double*>(h->ws + h->off_part);
   a.out = reinterpret_cast<double*>(h->ws + h->off_out);
   a.nx = p.nx;
@@ -662,7 +691,7 @@ int reduce_launch(ltne_handle* h) {
   a.sigma = p.sigma;
   a.qf = p.qf;
   a.qs = p.qs;
-  a.update_prev = 1;
+  a.update_prev = 0;  // the snapshot is a whole macro set (see ltne_observables)
   a.blocks = h->red_blocks;
   a.is_double = h->ec == 8;
   if (h->slab) {
@@ -686,6 +715,10 @@ int reduce_handle(ltne_handle* h, double* acc) {
   cudaError_t e = cudaMemcpyAsync(acc, h->ws + h->off_out, NACC * sizeof(double),
                                   cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) {  // these fields are the next residual's reference
+    h->msnap = h->mcur;
+    h->fused_valid = false;
+  }
   return fail_cuda(e);
 }
 
@@ -870,8 +903,28 @@ int ltne_step(ltne_handle* h, int64_t n) {
     ++h->step;
     ++h->launches;
   }
-  e = launch_step(h, h->cur, 1, h->stream, chained);
+  // the last step writes the fields and, unless the launch shape's grid
+  // outgrows the partials' room or the tiles are staged, the observables'
+  // block partials against the residual snapshot
+  begin_macro_write(h);
+  LatticeArgs a = lattice_args(h, h->cur, 1);
+  a.chained = chained ? 1 : 0;
+  const int64_t blocks = step_blocks(h);
+  const bool fuse = !h->shape.tma && blocks <= h->fpart_cap;
+  if (fuse) {
+    a.obs_part = reinterpret_cast<double*>(h->ws + h->off_fpart);
+    a.obs_prev = h->msnap >= 0 ? h->ws + h->off_mac[h->msnap] + (size_t)h->plane * h->ec
+                               : nullptr;
+  }
+  switch (h->p.storage) {
+    case LTNE_F64: e = launch_step_f64(a, h->P, h->shape, h->stream); break;
+    case LTNE_F32: e = launch_step_f32(a, h->P, h->shape, h->stream); break;
+    case LTNE_F16DEV: e = launch_step_f16(a, h->P, h->shape, h->stream); break;
+    default: e = launch_step_bf16(a, h->P, h->shape, h->stream); break;
+  }
   if (e != cudaSuccess) return fail_cuda(e);
+  h->fused_valid = fuse;
+  h->fused_blocks = blocks;
   h->cur ^= 1;
   ++h->step;
   ++h->launches;
@@ -891,8 +944,15 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
       return fail_cuda(e);
     }
   }
-  const int rr = reduce_launch(h);
-  if (rr != LTNE_OK) return rr;
+  if (h->fused_valid) {  // the last step left the block partials
+    e = launch_reduce_partials(reinterpret_cast<const double*>(h->ws + h->off_fpart),
+                               h->fused_blocks, reinterpret_cast<double*>(h->ws + h->off_fpart2),
+                               reinterpret_cast<double*>(h->ws + h->off_out), h->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+  } else {
+    const int rr = reduce_launch(h);
+    if (rr != LTNE_OK) return rr;
+  }
   // the accumulators and the device error word in one read-back: a staged
   // step that gave up waiting for its tile reports here (the fields are then
   // not trustworthy); the word is cleared
@@ -915,8 +975,10 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   info.L = h->L;
   info.nu_f = h->nu_f;
   info.alpha_f = h->alpha_f;
-  const int rc = finish_observables(p, info, h->step, h->have_prev, acc, out);
+  const int rc = finish_observables(p, info, h->step, h->msnap >= 0, acc, out);
   h->have_prev = true;
+  h->msnap = h->mcur;  // these fields are the next residual's reference
+  h->fused_valid = false;
   return rc;
 }
 
@@ -931,7 +993,7 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
     const double ref = (k == 0) ? 1.0 : (k >= 3 ? p.T_ref : 0.0);  // planes hold deviations
     double* out = dst[k];
     const int rc = download_field(
-        h, h->ws + h->off_mac + (size_t)k * h->plane * h->ec, [&](const char* buf, int y0, int y1) {
+        h, mac_cur(h) + (size_t)k * h->plane * h->ec, [&](const char* buf, int y0, int y1) {
           const int64_t base = (int64_t)y0 * nx, cnt = (int64_t)(y1 - y0) * nx;
           if (h->ec == 8) {
             const double* t = reinterpret_cast<const double*>(buf);
@@ -974,7 +1036,7 @@ int ltne_get_state(ltne_handle* h, void* host, size_t bytes) {
   cudaError_t e = cudaMemcpyAsync(dst, h->ws + h->off_pop[h->cur], pb, cudaMemcpyDeviceToHost,
                                   h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dst + pb, h->ws + h->off_mac, mb, cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemcpyAsync(dst + pb, mac_cur(h), mb, cudaMemcpyDeviceToHost, h->stream);
   const size_t ub = h->p.hv_local ? (size_t)h->plane * h->ec : 0;
   if (e == cudaSuccess && ub)
     e = cudaMemcpyAsync(dst + pb + mb, h->ws + h->off_um[h->cur], ub, cudaMemcpyDeviceToHost,
@@ -996,10 +1058,13 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
     return LTNE_ERR_INVALID_ARG;
   const char* src = static_cast<const char*>(host) + 64;
   const size_t pb = 19 * (size_t)h->plane * h->es, mb = 5 * (size_t)h->plane * h->ec;
+  h->mcur = 0;  // the restored fields in macro set 0; no residual snapshot
+  h->msnap = -1;
+  h->fused_valid = false;
   cudaError_t e = cudaMemcpyAsync(h->ws + h->off_pop[0], src, pb, cudaMemcpyHostToDevice,
                                   h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->ws + h->off_mac, src + pb, mb, cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(mac_cur(h), src + pb, mb, cudaMemcpyHostToDevice, h->stream);
   const size_t ub = h->p.hv_local ? (size_t)h->plane * h->ec : 0;
   if (e == cudaSuccess && ub)
     e = cudaMemcpyAsync(h->ws + h->off_um[0], src + pb + mb, ub, cudaMemcpyHostToDevice,
@@ -1114,11 +1179,12 @@ int ltne_step_slabs(ltne_handle* h, int32_t nslabs, int64_t n, void* scratch, si
   if (e != cudaSuccess) return fail_cuda(e);
   // gather the computed rows and the macroscopic fields of the last step
   const int out = h->cur ^ (int)(n & 1);
+  begin_macro_write(h);
   for (const SlabGeom& s : g) {
     e = copy_rows(h->ws + h->off_pop[out], h->plane, s.g0, ws + s.off_pop[b], s.plane, s.lo,
                   s.rows, 19, pitch, es, st);
     if (e == cudaSuccess)
-      e = copy_rows(h->ws + h->off_mac, h->plane, s.g0, ws + s.off_mac, s.plane, s.lo, s.rows, 5,
+      e = copy_rows(mac_cur(h), h->plane, s.g0, ws + s.off_mac, s.plane, s.lo, s.rows, 5,
                     pitch, ec, st);
     if (e != cudaSuccess) return fail_cuda(e);
   }
@@ -1217,6 +1283,7 @@ int ltne_halo_unpack(ltne_handle* h) {
 int ltne_step_slab(ltne_handle* h, int32_t write_macros) {
   if (!h || !h->slab || (write_macros != 0 && write_macros != 1)) return LTNE_ERR_INVALID_ARG;
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
+  if (write_macros) begin_macro_write(h);
   const cudaError_t e = launch_step(h, h->cur, write_macros, h->stream);
   if (e != cudaSuccess) return fail_cuda(e);
   h->cur ^= 1;

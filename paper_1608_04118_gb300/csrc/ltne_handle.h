@@ -18,7 +18,14 @@ struct ltne_handle {
   // layout
   int64_t pitch = 0, plane = 0;
   size_t es = 0, ec = 0;  // storage / compute element sizes
-  size_t off_pop[2] = {0, 0}, off_phi = 0, off_mac = 0, off_prev = 0, off_part = 0, off_out = 0;
+  size_t off_pop[2] = {0, 0}, off_phi = 0, off_part = 0, off_out = 0;
+  // two sets of the 5 macro planes: the current state's, and the snapshot
+  // taken by the last ltne_observables call (the residual's reference)
+  size_t off_mac[2] = {0, 0};
+  // block partials of the observables accumulated by the last step of an
+  // ltne_step call, and the first level of their combination
+  size_t off_fpart = 0, off_fpart2 = 0;
+  int64_t fpart_cap = 0;   // blocks the fused partials have room for
   size_t off_tick = 0;
   size_t off_um[2] = {0, 0};  // |u| planes (local h_v of Eq. 52)
   size_t ws_bytes = 0;
@@ -29,6 +36,10 @@ struct ltne_handle {
   int64_t step = 0;
   bool fields_set = false;
   bool have_prev = false;
+  int mcur = 0;             // macro set holding the current state's fields
+  int msnap = -1;           // macro set holding the snapshot (-1: none yet)
+  bool fused_valid = false; // the fused partials describe the current state
+  int64_t fused_blocks = 0; // and how many blocks wrote them
   float enc_scale = 1.0f;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t launches = 0;
@@ -53,6 +64,13 @@ struct ltne_handle {
 };
 
 namespace ltne {
+// The current state's macro planes.
+inline char* mac_cur(const ltne_handle* h) { return h->ws + h->off_mac[h->mcur]; }
+// The macro set the next write of the fields goes to: never the snapshot
+// of the last observables call while the residual still needs it.
+inline int mac_next(const ltne_handle* h) {
+  return h->msnap == h->mcur ? (h->mcur ^ 1) : h->mcur;
+}
 // Initial state S_0 from host fields (ltne_set_fields); pre_out, if not
 // null, also receives S_0 (compute type, population-plane layout).
 int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, const double* ux,

@@ -4,14 +4,18 @@
 //
 // Two passes with a fixed summation order, so results are bitwise
 // reproducible for a given lattice size: pass 1 writes one partial vector per
-// block (RB columns x seg rows) into a scratch buffer; pass 2 (one block)
-// reduces the partials in block order.  Per-node terms are accumulated in
-// the fields' precision over at most seg nodes per thread and across the 32
-// threads of a warp (FP64 on GB300 runs at a small fraction of the FP32
-// rate, so FP64 per node -- or a warp shuffle tree in FP64 in every block --
-// would make this pass compute-bound); every combination above that, the
-// warps of a block and the blocks, is FP64.
-#include "ltne_internal.h"
+// block (RB columns x seg rows) into a scratch buffer; pass 2 reduces the
+// partials in block order.  Per-node terms of FP32 fields are summed over at
+// most seg nodes per thread and across the 32 threads of a warp as two-part
+// FP32 sums (error-free additions, ltne_obs.cuh): FP64 on GB300 runs at a
+// small fraction of the FP32 rate, so FP64 per node -- or a warp shuffle
+// tree in FP64 in every block -- would make this pass compute-bound, while
+// the two-part sums carry about 48 significant bits at FP32 speed; every
+// combination above the warp, the warps of a block and the blocks, is FP64.
+// This pass serves the states whose last step did not accumulate the
+// observables itself (after set_fields, a checkpoint restore, the slab and
+// adjoint paths, the batched form and the allocation-free entry point).
+#include "ltne_obs.cuh"
 
 namespace ltne {
 
@@ -28,7 +32,6 @@ int reduce_seg(int nx, int ny) {
   return 64;
 }
 
-__device__ __forceinline__ float cmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double cmax(double a, double b) { return fmax(a, b); }
 
 template <typename C>
@@ -61,18 +64,16 @@ __device__ void block_reduce(double (&acc)[NACC], double* sh /* [RB/32][NACC] */
 
 // Pass 1.  Block (RB threads) covers RB consecutive columns and seg rows;
 // each thread walks its column down the segment (coalesced rows across the
-// warp), accumulating in the fields' own precision C over at most seg nodes
-// and across the warp, then the warp partials and everything above in FP64.
-// Rows go in groups of RU (4 in FP32, 2 in FP64, which holds twice the
+// warp) and accumulates its nodes' terms (obs_node) as two-part FP32 sums,
+// then the warp, then the warps' partials in FP64 (obs_block_store).  Rows
+// go in groups of RU (4 in FP32, 2 in FP64, which holds twice the
 // registers per value): all loads of a group are issued before any of its
 // snapshot stores, so a thread keeps RU rows of loads in flight.
 template <typename C>
 __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
   constexpr int RU = sizeof(C) == 4 ? 4 : 2;
-  __shared__ double sh[(RB / 32) * NACC];
-  C acc[NACC];
-#pragma unroll
-  for (int k = 0; k < NACC; ++k) acc[k] = C(0);
+  ObsAcc<C> acc;
+  obs_zero(acc);
   const C* __restrict__ mac = static_cast<const C*>(a.mac);
   const C* __restrict__ phi_f = static_cast<const C*>(a.phi);
   C* __restrict__ prev = static_cast<C*>(a.prev);
@@ -81,10 +82,6 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
   const int y0 = blockIdx.y * seg;
   const int y1 = min(y0 + seg, a.ny);
   const C phi_u = C(a.phi_u), sigma = C(a.sigma);
-  // Wall-flux stencil weights: q_hot = 1.5 T_h - 2 T(1,y) + 0.5 T(2,y),
-  // q_cold = -1.5 T_c + 2 T(nx-2,y) - 0.5 T(nx-3,y), trapezoid rule in y.
-  const C whot = (x == 1) ? C(-2) : (x == 2) ? C(0.5) : C(0);
-  const C wcold = (x == a.nx - 2) ? C(2) : (x == a.nx - 3) ? C(-0.5) : C(0);
   if (x < a.nx) {
     for (int yg = y0; yg < y1; yg += RU) {
       // deviations: rho - 1, ux, uy, T_f - T0, T_s - T0; the previous
@@ -110,30 +107,8 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
         const int y = yg + r;
         if (y >= y1) break;
         const C wy = ((y == 0 && a.wall_lo) || (y == a.ny - 1 && a.wall_hi)) ? C(0.5) : C(1);
-        acc[A_NUF_H] += whot * wy * Tf[r];
-        acc[A_NUS_H] += whot * wy * Ts[r];
-        acc[A_NUF_C] += wcold * wy * Tf[r];
-        acc[A_NUS_C] += wcold * wy * Ts[r];
-        acc[A_MASS] += rho[r];
-        // deviation part of phi T_f + (1-phi) sigma T_s; the T0 and Q parts
-        // are restored from the porosity sum in FP64
-        acc[A_ENERGY] += phi[r] * Tf[r] + (C(1) - phi[r]) * sigma * Ts[r];
-        acc[A_SUMPHI] += phi[r];
-        const C u2 = ux[r] * ux[r] + uy[r] * uy[r];
-        acc[A_MAXU] = u2 > acc[A_MAXU] ? u2 : acc[A_MAXU];  // |u|^2, rooted in FP64
-        const C dT = Tf[r] > Ts[r] ? Tf[r] - Ts[r] : Ts[r] - Tf[r];
-        acc[A_MAXDT] = dT > acc[A_MAXDT] ? dT : acc[A_MAXDT];
-        acc[A_SUMTF] += Tf[r];
-        acc[A_SUMTS] += Ts[r];
-        acc[A_DU2] += (ux[r] - pux[r]) * (ux[r] - pux[r]) + (uy[r] - puy[r]) * (uy[r] - puy[r]);
-        acc[A_U2] += u2;
-        acc[A_DTF2] += (Tf[r] - pTf[r]) * (Tf[r] - pTf[r]);
-        acc[A_TF2] += Tf[r] * Tf[r];
-        acc[A_DTS2] += (Ts[r] - pTs[r]) * (Ts[r] - pTs[r]);
-        acc[A_TS2] += Ts[r] * Ts[r];
-        if (!(isfinite(rho[r]) && isfinite(ux[r]) && isfinite(uy[r]) && isfinite(Tf[r]) &&
-              isfinite(Ts[r])))
-          acc[A_BAD] += C(1);
+        obs_node<C>(acc, rho[r], ux[r], uy[r], Tf[r], Ts[r], phi[r], sigma, pux[r], puy[r],
+                    pTf[r], pTs[r], wy, x, a.nx);
       }
       if (a.update_prev) {
 #pragma unroll
@@ -149,47 +124,28 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
       }
     }
   }
-  // the warp in the fields' precision (fixed shuffle order), then the warp
-  // partials in FP64 in warp order
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NACC; ++k) {
-    C v = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = combine<C>(k, v, __shfl_down_sync(0xffffffffu, v, o));
-    acc[k] = v;
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NACC; ++k) sh[warp * NACC + k] = (double)acc[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double dacc[NACC];
-#pragma unroll
-    for (int k = 0; k < NACC; ++k) dacc[k] = sh[k];
-    for (int w = 1; w < RB / 32; ++w)
-#pragma unroll
-      for (int k = 0; k < NACC; ++k) dacc[k] = combine<double>(k, dacc[k], sh[w * NACC + k]);
-    const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll
-    for (int k = 0; k < NACC; ++k) a.partials[b * NACC + k] = dacc[k];
-  }
+  obs_block_store<C>(acc, a.partials);
 }
 
+// Block b combines partial vectors [b * chunk, min((b + 1) * chunk, blocks))
+// into out[b] (fixed order: thread strides, then the block tree).
 __global__ void __launch_bounds__(RB) k_reduce_pass2(const double* __restrict__ partials,
-                                                     int blocks, double* __restrict__ out) {
+                                                     int64_t blocks, int64_t chunk,
+                                                     double* __restrict__ out) {
   __shared__ double sh[(RB / 32) * NACC];
   double acc[NACC];
 #pragma unroll
   for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < blocks; b += RB)
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < blocks ? b0 + chunk : blocks;
+  for (int64_t b = b0 + threadIdx.x; b < b1; b += RB)
 #pragma unroll
     for (int k = 0; k < NACC; ++k)
-      acc[k] = combine<double>(k, acc[k], partials[(int64_t)b * NACC + k]);
+      acc[k] = combine<double>(k, acc[k], partials[b * NACC + k]);
   block_reduce(acc, sh);
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) out[k] = acc[k];
+    for (int k = 0; k < NACC; ++k) out[(int64_t)blockIdx.x * NACC + k] = acc[k];
 }
 
 }  // namespace
@@ -209,7 +165,21 @@ cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
     k_reduce_pass1<float><<<grid, RB, 0, st>>>(a, seg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_reduce_pass2<<<1, RB, 0, st>>>(a.partials, a.blocks, a.out);
+  k_reduce_pass2<<<1, RB, 0, st>>>(a.partials, a.blocks, a.blocks, a.out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* partials, int64_t blocks, double* level,
+                                   double* out, cudaStream_t st) {
+  if (blocks <= kObsChunk) {
+    k_reduce_pass2<<<1, RB, 0, st>>>(partials, blocks, blocks, out);
+    return cudaGetLastError();
+  }
+  const int64_t g = (blocks + kObsChunk - 1) / kObsChunk;
+  k_reduce_pass2<<<(unsigned)g, RB, 0, st>>>(partials, blocks, kObsChunk, level);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_reduce_pass2<<<1, RB, 0, st>>>(level, g, g, out);
   return cudaGetLastError();
 }
 
