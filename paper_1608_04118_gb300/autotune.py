@@ -52,14 +52,16 @@ def tune_batch(batch, steps=8, warmup=2):
 
 
 # Single-lattice step kernel: block shapes (threads per block <= 256) and
-# nodes per thread (2 = paired FP32 arithmetic, not for FP64 storage).
+# nodes per thread (2 = paired FP32 arithmetic, not for FP64 storage; 4 and 8
+# = a node pair in 2 or 4 consecutive rows, 16-bit storage of a cavity).
 CAVITY_SHAPES = ((32, 2), (32, 4), (64, 1), (64, 2), (64, 4), (128, 1), (128, 2), (256, 1))
 
 
 def cavity_candidates(storage):
-    for npt in ((1,) if storage == "f64" else (1, 2)):
+    npts = (1,) if storage == "f64" else ((1, 2, 4, 8) if storage in ("f16", "bf16") else (1, 2))
+    for npt in npts:
         for bx, by in CAVITY_SHAPES:
-            if npt == 1 or bx * by <= 128:  # the two-node kernel takes <= 128 threads
+            if npt == 1 or bx * by <= 128:  # the two-node kernels take <= 128 threads
                 yield bx, by, npt
 
 
@@ -69,9 +71,14 @@ def tune_cavity(cav, steps=20, warmup=4):
     seconds per step, table of all trials)."""
     import torch
 
+    from .ltne import LtneError
+
     table = []
     for sch in cavity_candidates(cav.storage):
-        cav.set_schedule(*sch)
+        try:
+            cav.set_schedule(*sch)
+        except LtneError:  # a form this lattice does not take (e.g. rows without cavity walls)
+            continue
         with torch.cuda.stream(cav.stream):
             cav.step(warmup)
             e0 = torch.cuda.Event(enable_timing=True)

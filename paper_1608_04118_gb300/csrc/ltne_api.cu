@@ -466,16 +466,6 @@ void layout(ltne_handle* h) {
   off = align_up(off + (size_t)h->red_blocks * NACC * sizeof(double), A);
   h->off_out = off;
   off = align_up(off + NACC * sizeof(double), A);
-  // block partials of the observables fused into the last step of a call:
-  // room for the grids of the default launch shapes (64 x 2 one node per
-  // thread; two nodes per thread in 128 x 1 or 32 x 4), and for the first
-  // level of their combination
-  h->fpart_cap = (int64_t)((p.nx + 63) / 64) * ((p.ny + 1) / 2);
-  h->off_fpart = off;
-  off = align_up(off + (size_t)h->fpart_cap * NACC * sizeof(double), A);
-  h->off_fpart2 = off;
-  off = align_up(off + (size_t)((h->fpart_cap + kObsChunk - 1) / kObsChunk) * NACC *
-                           sizeof(double), A);
   h->off_tick = off;  // two uint32 step counters for the stochastic rounding, then
   off = align_up(off + 3 * sizeof(uint32_t), A);  // the device error word
   for (int b = 0; b < 2; ++b) {  // |u| of the previous state per buffer (Eq. 52)
@@ -528,18 +518,8 @@ cudaError_t launch_step(ltne_handle* h, int src_buf, int write_macros, cudaStrea
 }
 
 // Point the current macro set at the one the next write of the fields
-// goes to (never the residual snapshot) and forget the fused partials.
-void begin_macro_write(ltne_handle* h) {
-  h->mcur = mac_next(h);
-  h->fused_valid = false;
-}
-
-// Blocks of the step grid for the handle's launch shape.
-int64_t step_blocks(const ltne_handle* h) {
-  const int64_t cols = h->shape.pair ? (h->p.nx + 1) / 2 : h->p.nx;
-  return ((cols + h->shape.bx - 1) / h->shape.bx) * (((int64_t)h->p.ny + h->shape.by - 1) /
-                                                      h->shape.by);
-}
+// goes to (never the residual snapshot).
+void begin_macro_write(ltne_handle* h) { h->mcur = mac_next(h); }
 
 void drop_graphs(ltne_handle* h) {
   for (auto& g : h->graph)
@@ -644,7 +624,6 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   };
   h->mcur = 0;  // the fields go to macro set 0; no residual snapshot yet
   h->msnap = -1;
-  h->fused_valid = false;
   for (int k = 0; k < 5; ++k) {
     if (!src[k]) continue;
     rc = stage(src[k], defaults[k], refs[k], mac_cur(h) + (size_t)k * h->plane * h->ec);
@@ -715,10 +694,7 @@ int reduce_handle(ltne_handle* h, double* acc) {
   cudaError_t e = cudaMemcpyAsync(acc, h->ws + h->off_out, NACC * sizeof(double),
                                   cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess) {  // these fields are the next residual's reference
-    h->msnap = h->mcur;
-    h->fused_valid = false;
-  }
+  if (e == cudaSuccess) h->msnap = h->mcur;  // these fields are the next residual's reference
   return fail_cuda(e);
 }
 
@@ -903,28 +879,9 @@ int ltne_step(ltne_handle* h, int64_t n) {
     ++h->step;
     ++h->launches;
   }
-  // the last step writes the fields and, unless the launch shape's grid
-  // outgrows the partials' room or the tiles are staged, the observables'
-  // block partials against the residual snapshot
-  begin_macro_write(h);
-  LatticeArgs a = lattice_args(h, h->cur, 1);
-  a.chained = chained ? 1 : 0;
-  const int64_t blocks = step_blocks(h);
-  const bool fuse = !h->shape.tma && blocks <= h->fpart_cap;
-  if (fuse) {
-    a.obs_part = reinterpret_cast<double*>(h->ws + h->off_fpart);
-    a.obs_prev = h->msnap >= 0 ? h->ws + h->off_mac[h->msnap] + (size_t)h->plane * h->ec
-                               : nullptr;
-  }
-  switch (h->p.storage) {
-    case LTNE_F64: e = launch_step_f64(a, h->P, h->shape, h->stream); break;
-    case LTNE_F32: e = launch_step_f32(a, h->P, h->shape, h->stream); break;
-    case LTNE_F16DEV: e = launch_step_f16(a, h->P, h->shape, h->stream); break;
-    default: e = launch_step_bf16(a, h->P, h->shape, h->stream); break;
-  }
+  begin_macro_write(h);  // the last step writes the fields
+  e = launch_step(h, h->cur, 1, h->stream, chained);
   if (e != cudaSuccess) return fail_cuda(e);
-  h->fused_valid = fuse;
-  h->fused_blocks = blocks;
   h->cur ^= 1;
   ++h->step;
   ++h->launches;
@@ -944,15 +901,8 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
       return fail_cuda(e);
     }
   }
-  if (h->fused_valid) {  // the last step left the block partials
-    e = launch_reduce_partials(reinterpret_cast<const double*>(h->ws + h->off_fpart),
-                               h->fused_blocks, reinterpret_cast<double*>(h->ws + h->off_fpart2),
-                               reinterpret_cast<double*>(h->ws + h->off_out), h->stream);
-    if (e != cudaSuccess) return fail_cuda(e);
-  } else {
-    const int rr = reduce_launch(h);
-    if (rr != LTNE_OK) return rr;
-  }
+  const int rr = reduce_launch(h);
+  if (rr != LTNE_OK) return rr;
   // the accumulators and the device error word in one read-back: a staged
   // step that gave up waiting for its tile reports here (the fields are then
   // not trustworthy); the word is cleared
@@ -978,7 +928,6 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   const int rc = finish_observables(p, info, h->step, h->msnap >= 0, acc, out);
   h->have_prev = true;
   h->msnap = h->mcur;  // these fields are the next residual's reference
-  h->fused_valid = false;
   return rc;
 }
 
@@ -1060,7 +1009,6 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
   const size_t pb = 19 * (size_t)h->plane * h->es, mb = 5 * (size_t)h->plane * h->ec;
   h->mcur = 0;  // the restored fields in macro set 0; no residual snapshot
   h->msnap = -1;
-  h->fused_valid = false;
   cudaError_t e = cudaMemcpyAsync(h->ws + h->off_pop[0], src, pb, cudaMemcpyHostToDevice,
                                   h->stream);
   if (e == cudaSuccess)
@@ -1106,13 +1054,20 @@ int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
   const int64_t threads = (int64_t)block_x * block_y;
   if (block_x < 32 || block_x > 256 || block_x % 32 != 0 || block_y < 1 || threads > 256)
     return LTNE_ERR_INVALID_ARG;
-  if (nodes_per_thread != 1 && nodes_per_thread != 2) return LTNE_ERR_INVALID_ARG;
-  if (nodes_per_thread == 2 &&
+  if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4 &&
+      nodes_per_thread != 8)
+    return LTNE_ERR_INVALID_ARG;
+  if (nodes_per_thread >= 2 &&
       (h->p.storage == LTNE_F64 || threads > kPairBlockThreads || h->slab))
+    return LTNE_ERR_INVALID_ARG;
+  // 4 / 8: a node pair in 2 / 4 consecutive rows (16-bit storage, cavity walls)
+  if (nodes_per_thread >= 4 && ((h->p.storage != LTNE_F16DEV && h->p.storage != LTNE_BF16DEV) ||
+                                h->p.bc != LTNE_BC_CAVITY))
     return LTNE_ERR_INVALID_ARG;
   h->shape.bx = block_x;
   h->shape.by = block_y;
-  h->shape.pair = nodes_per_thread == 2 ? 1 : 0;
+  h->shape.pair = nodes_per_thread >= 2 ? 1 : 0;
+  h->shape.rows = nodes_per_thread >= 4 ? nodes_per_thread / 2 : 1;
   drop_graphs(h);  // the captured launches carry the old configuration
   return LTNE_OK;
 }
@@ -1347,7 +1302,7 @@ int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
   if (!h || !block_x || !block_y || !nodes_per_thread) return LTNE_ERR_INVALID_ARG;
   *block_x = h->shape.bx;
   *block_y = h->shape.by;
-  *nodes_per_thread = h->shape.pair ? 2 : 1;
+  *nodes_per_thread = h->shape.pair ? 2 * h->shape.rows : 1;
   return LTNE_OK;
 }
 

@@ -40,12 +40,6 @@ struct LatticeArgs {
   int* err;                 // device error word: set by a bounded wait that gave up
   int slab_walls;           // BC_SLAB: which of the first / last rows are walls
   int chained;              // launch as a programmatic dependent of the stream's last kernel
-  // Observables fused into this step (write_macros = 1 only): obs_part
-  // receives one FP64 partial vector per block, obs_prev points at the
-  // snapshot's u_x plane (u_x, u_y, T_f - T0, T_s - T0 at plane stride), or
-  // null when there is no snapshot (the residual's differences are then 0).
-  double* obs_part;
-  const void* obs_prev;
 };
 
 // Programmatic dependent launch.  A kernel launched with programmatic
@@ -87,7 +81,10 @@ struct StepShape {
   int bx = 64;
   int by = 2;
   int pair = 0;
-  int tma = 0;  // two nodes per thread from TMA-staged tiles (cavity walls only)
+  int tma = 0;   // two nodes per thread from TMA-staged tiles (cavity walls only)
+  int rows = 1;  // > 1: a pair of nodes in several consecutive rows per thread,
+                 // the next row's loads ahead of this row's arithmetic (16-bit
+                 // storage with cavity walls; the same bits as rows = 1)
 };
 
 // Per-storage-type launchers (one translation unit each).
@@ -127,11 +124,6 @@ struct ReduceArgs {
 };
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
-// Combine `blocks` FP64 partial vectors (in block order) into out[NACC]:
-// blocks of up to kObsChunk vectors first into level[], then those.
-constexpr int kObsChunk = 1024;
-cudaError_t launch_reduce_partials(const double* partials, int64_t blocks, double* level,
-                                   double* out, cudaStream_t st);
 
 // Halo rows of a row slab (ltne_slab.cu).  Pack: the populations of the
 // slab's first computed row that stream down (e_y = -1: f_4, f_7, f_8,

@@ -1,18 +1,15 @@
-// ltne_obs.cuh -- the observables' per-block partial sums, accumulated by
-// the last time step of an ltne_step() call while it holds the macroscopic
-// values in registers (the step writes them to the macro planes anyway), so
-// that ltne_observables() only combines the block partials.
+// ltne_obs.cuh -- per-node terms of the observables and their per-block
+// combination, for the reduction pass of ltne_reduce.cu.
 //
-// Per node, the same terms as the stand-alone reduction of ltne_reduce.cu:
-// the wall-flux stencils of Nu (second-order one-sided difference,
+// Per node: the wall-flux stencils of Nu (second-order one-sided difference,
 // trapezoid rule in y), mass, energy, the sums and squares of the residual,
-// the maxima of |u|^2 and |T_f - T_s|, a non-finite count.  A thread holds
-// one or two nodes; the 32 lanes of a warp are combined as unevaluated sums
-// of two FP32 values (hi + lo, each addition and its renormalisation
+// the maxima of |u|^2 and |T_f - T_s|, a non-finite count.  For FP32 fields
+// a thread's terms and the 32 lanes of a warp are combined as unevaluated
+// sums of two FP32 values (hi + lo, each addition and its renormalisation
 // error-free by Knuth's TwoSum), so the warp sums carry about 48
 // significant bits; from the warp partials upward every sum is FP64, in a
 // fixed order (warps of a block, then blocks: bitwise reproducible for a
-// given launch shape).  FP64 storage accumulates in FP64 throughout.
+// given lattice).  FP64 fields accumulate in FP64 throughout.
 #pragma once
 
 #include "ltne_internal.h"

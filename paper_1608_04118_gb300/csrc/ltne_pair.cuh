@@ -220,17 +220,10 @@ __device__ __forceinline__ void st_f2(float* __restrict__ p, F2 v) {
   *reinterpret_cast<float2*>(p) = v.v;
 }
 
-// Observables terms of the pair (x0, y), (x0 + 1, y) (OBS kernels).
-struct PairObs {
-  ObsAcc<float>* acc;
-  const float* prev;  // residual snapshot's u_x plane, or null
-  int x0, y, nx, ny;
-};
-
 // Everything after the pull for a pair at element offset off whose
 // pre-collision values are in f, gf, gs: macroscopic values, collision,
 // stores.  Shared by the pull from HBM and the pull from a staged tile.
-template <typename S, bool OBS = false>
+template <typename S>
 __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
                                             const float* __restrict__ phi_field,
                                             float* __restrict__ mac, const NodeParams<F2>& P,
@@ -238,7 +231,7 @@ __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
                                             const float scale, const int write_macros,
                                             const uint32_t tick, const float* __restrict__ um_in,
                                             float* __restrict__ um_out, F2 (&f)[9], F2 (&gf)[5],
-                                            F2 (&gs)[5], const PairObs* ob = nullptr) {
+                                            F2 (&gs)[5]) {
   Medium<F2> md = phi_field ? medium_at<F2>(P, ld_f2(phi_field + off)) : P.um;
   if (P.hv_local) set_exchange<F2>(md, hv_local_at<F2>(P, ld_f2(um_in + off)));
   Macro<F2> m;
@@ -251,20 +244,6 @@ __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
     st_f2(mac + 3u * pl + off, m.dTf);
     st_f2(mac + 4u * pl + off, m.dTs);
   }
-  if constexpr (OBS) {
-    F2 pux = m.ux, puy = m.uy, pTf = m.dTf, pTs = m.dTs;
-    if (ob->prev) {
-      pux = ld_f2(ob->prev + off);
-      puy = ld_f2(ob->prev + pl + off);
-      pTf = ld_f2(ob->prev + 2u * pl + off);
-      pTs = ld_f2(ob->prev + 3u * pl + off);
-    }
-    const float wy = (ob->y == 0 || ob->y == ob->ny - 1) ? 0.5f : 1.0f;
-    obs_node<float>(*ob->acc, m.drho.v.x, m.ux.v.x, m.uy.v.x, m.dTf.v.x, m.dTs.v.x, md.phi.v.x,
-                    P.sigma.v.x, pux.v.x, puy.v.x, pTf.v.x, pTs.v.x, wy, ob->x0, ob->nx);
-    obs_node<float>(*ob->acc, m.drho.v.y, m.ux.v.y, m.uy.v.y, m.dTf.v.y, m.dTs.v.y, md.phi.v.y,
-                    P.sigma.v.y, pux.v.y, puy.v.y, pTf.v.y, pTs.v.y, wy, ob->x0 + 1, ob->nx);
-  }
   collide<F2>(P, m, f, gf, gs);
   PairPops<S>::store(dst, pl, off, scale, f, gf, gs, off, tick);
 }
@@ -272,7 +251,7 @@ __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
 // The pair (x0, y), (x0 + 1, y) when both nodes exist and neither is a
 // left/right wall node: interior nodes, or both on a no-slip adiabatic row
 // (same rebuild, from the row above or below).
-template <typename S, int BC, bool OBS = false>
+template <typename S, int BC>
 __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restrict__ dst,
                                           const float* __restrict__ phi_field,
                                           float* __restrict__ mac, const NodeParams<F2>& P,
@@ -280,8 +259,7 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
                                           const uint32_t pi, const uint32_t pl, const float scale,
                                           const float inv_scale, const int write_macros,
                                           const uint32_t tick, const float* __restrict__ um_in,
-                                          float* __restrict__ um_out,
-                                          const PairObs* ob = nullptr) {
+                                          float* __restrict__ um_out) {
   int cy = y;
   bool wall_row = false;
   if (BC == BC_CAVITY || BC == BC_CHANNEL) {
@@ -311,8 +289,8 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
     macros<F2>(P, mdn, f, gf, gs, mn);
     nee<F2>(P, mn, mn.dTf, mn.dTs, f, gf, gs);  // adiabatic: the neighbour's temperatures
   }
-  finish_pair<S, OBS>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out,
-                      f, gf, gs, ob);
+  finish_pair<S>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out, f, gf,
+                 gs);
 }
 
 // A cavity pair holding a left or right wall node (x0 = 0, or x0 + 1 =
@@ -325,7 +303,7 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
 // lanes continue as any pair.  The same rebuild as the one-node step, in
 // paired arithmetic, without the warp divergence of two one-node steps
 // beside the pairs of the rest of the row.
-template <typename S, bool OBS = false>
+template <typename S>
 __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __restrict__ dst,
                                                const float* __restrict__ phi_field,
                                                float* __restrict__ mac, const NodeParams<F2>& P,
@@ -334,8 +312,7 @@ __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __r
                                                const float scale, const float inv_scale,
                                                const int write_macros, const uint32_t tick,
                                                const float* __restrict__ um_in,
-                                               float* __restrict__ um_out,
-                                               const PairObs* ob = nullptr) {
+                                               float* __restrict__ um_out) {
   const bool left = x0 == 0;
   const bool wall_row = y == 0 || y == ny - 1;
   const int cx = left ? 1 : nx - 2;
@@ -393,8 +370,8 @@ __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __r
     gs[i] = pick(rgs[i], gs[i]);
   }
   const uint32_t off = (uint32_t)y * pi + (uint32_t)x0;
-  finish_pair<S, OBS>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out,
-                      f, gf, gs, ob);
+  finish_pair<S>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out, f, gf,
+                 gs);
 }
 
 // Register budget of the pair kernel: blocks of at most 128 threads and at
@@ -406,49 +383,17 @@ __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __r
 constexpr int kPairMaxThreads = kPairBlockThreads;
 constexpr int kPairMinBlocks = 5;
 
-// OBS: the last step of an ltne_step call with the observables' block
-// partials (its own instantiation, once per call: the register cap of the
-// plain form is lifted there, so that the accumulators do not spill).
-template <typename S, int BC, bool OBS>
-__global__ void __launch_bounds__(kPairMaxThreads, OBS ? 1 : kPairMinBlocks) k_step_pair(
+template <typename S, int BC>
+__global__ void __launch_bounds__(kPairMaxThreads, kPairMinBlocks) k_step_pair(
     const S* __restrict__ src, S* __restrict__ dst, const float* __restrict__ phi_field,
     float* __restrict__ mac, const NodeParams<F2> P, const NodeParams<float> P1, const int nx,
     const int ny, const int64_t pitch, const int64_t plane, const float scale,
     const float inv_scale, const int write_macros, const uint32_t* __restrict__ tick_in,
-    uint32_t* __restrict__ tick_out, const float* __restrict__ um_in, float* __restrict__ um_out,
-    double* __restrict__ obs_part, const float* __restrict__ obs_prev) {
+    uint32_t* __restrict__ tick_out, const float* __restrict__ um_in, float* __restrict__ um_out) {
   grid_dep_wait();
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t tick = read_tick<S, float>(tick_in, tick_out);
-  if constexpr (OBS) {
-    ObsAcc<float> acc;
-    obs_zero(acc);
-    const PairObs ob{&acc, obs_prev, x0, y, nx, ny};
-    if (x0 < nx && y < ny) {
-      const bool full = x0 + 1 < nx;
-      const bool uniform = BC == BC_CAVITY ? (x0 > 0 && x0 + 2 < nx) : full;
-      if (uniform) {
-        step_pair<S, BC, true>(src, dst, phi_field, mac, P, x0, y, nx, ny, (uint32_t)pitch,
-                               (uint32_t)plane, scale, inv_scale, write_macros, tick, um_in,
-                               um_out, &ob);
-      } else if (BC == BC_CAVITY && full) {
-        step_pair_side<S, true>(src, dst, phi_field, mac, P, x0, y, nx, ny, (uint32_t)pitch,
-                                (uint32_t)plane, scale, inv_scale, write_macros, tick, um_in,
-                                um_out, &ob);
-      } else {
-        step_node<S, float, BC, true>(src, dst, phi_field, mac, P1, x0, y, nx, ny, pitch, plane,
-                                      scale, inv_scale, write_macros, tick, nullptr, um_in,
-                                      um_out, 0, &acc, obs_prev);
-        if (full)
-          step_node<S, float, BC, true>(src, dst, phi_field, mac, P1, x0 + 1, y, nx, ny, pitch,
-                                        plane, scale, inv_scale, write_macros, tick, nullptr,
-                                        um_in, um_out, 0, &acc, obs_prev);
-      }
-    }
-    obs_block_store<float>(acc, obs_part);
-    return;
-  }
   if (x0 >= nx || y >= ny) return;
   const bool full = x0 + 1 < nx;
   const bool uniform = BC == BC_CAVITY ? (x0 > 0 && x0 + 2 < nx) : full;
@@ -464,6 +409,138 @@ __global__ void __launch_bounds__(kPairMaxThreads, OBS ? 1 : kPairMinBlocks) k_s
     if (full)
       step_node<S, float, BC>(src, dst, phi_field, mac, P1, x0 + 1, y, nx, ny, pitch, plane,
                               scale, inv_scale, write_macros, tick, nullptr, um_in, um_out);
+  }
+}
+
+// ---- 16-bit storage: one column pair over R consecutive rows ------------
+//
+// The two-node kernel above waits on its loads at 28 % warp occupancy (96
+// registers) and issues 58 % of the cycles.  Here a thread advances the
+// pair (x0, x0 + 1) in R consecutive rows and issues the 19 loads of row
+// y + 1 before the arithmetic of row y, so that one row's load latency is
+// covered by the previous row's work within the warp instead of by other
+// warps.  The loaded 16-bit values wait as 19 packed 32-bit words (even
+// node in the low half; the x-shifted pairs joined with one byte permute),
+// about 19 registers more than the plain form.  The arithmetic of a pair is
+// exactly that of the plain form (finish_pair), so both give the same bits.
+// Cavity walls only; wall rows and pairs holding a side-wall node take the
+// plain form's code.
+
+// The 19 values streaming into an interior pair, as packed 16-bit pairs.
+struct RawPair {
+  uint32_t w[19];
+};
+
+template <typename S>
+__device__ __forceinline__ void load_raw_pair(const S* __restrict__ src, uint32_t pl, uint32_t pi,
+                                              int x0, int y, RawPair& r) {
+  const uint16_t* __restrict__ s16 = reinterpret_cast<const uint16_t*>(src);
+  const uint32_t r0 = (uint32_t)y * pi, rm = r0 - pi, rp = r0 + pi;
+  const uint32_t a = (uint32_t)x0;
+  auto pair = [&](uint32_t k, uint32_t row) {
+    return *reinterpret_cast<const uint32_t*>(s16 + (k * pl + row + a));
+  };
+  auto left = [&](uint32_t k, uint32_t row) {  // columns x0 - 1, x0
+    const uint32_t q = k * pl + row + a;
+    return __byte_perm((uint32_t)s16[q - 1], (uint32_t)s16[q], 0x5410);
+  };
+  auto right = [&](uint32_t k, uint32_t row) {  // columns x0 + 1, x0 + 2
+    const uint32_t q = k * pl + row + a;
+    return __byte_perm((uint32_t)s16[q + 1], (uint32_t)s16[q + 2], 0x5410);
+  };
+  // the populations' source rows and columns as in PairPops::pull
+  r.w[0] = pair(0, r0);
+  r.w[1] = left(1, r0);
+  r.w[2] = pair(2, rm);
+  r.w[3] = right(3, r0);
+  r.w[4] = pair(4, rp);
+  r.w[5] = left(5, rm);
+  r.w[6] = right(6, rm);
+  r.w[7] = right(7, rp);
+  r.w[8] = left(8, rp);
+#pragma unroll
+  for (uint32_t t = 0; t < 2; ++t) {
+    const uint32_t k0 = t == 0 ? 9u : 14u;
+    r.w[k0] = pair(k0, r0);
+    r.w[k0 + 1] = left(k0 + 1, r0);
+    r.w[k0 + 2] = pair(k0 + 2, rm);
+    r.w[k0 + 3] = right(k0 + 3, r0);
+    r.w[k0 + 4] = pair(k0 + 4, rp);
+  }
+}
+
+template <typename S> __device__ __forceinline__ F2 dec_word(uint32_t w, float inv_scale);
+template <> __device__ __forceinline__ F2 dec_word<__half>(uint32_t w, float inv_scale) {
+  const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
+  return F2(mul2_(v, make_float2(inv_scale, inv_scale)));
+}
+template <> __device__ __forceinline__ F2 dec_word<__nv_bfloat16>(uint32_t w, float) {
+  return F2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+// Resident blocks asked of the compiler for the row-pipelined form with 2
+// and with 4 rows per thread (the register budget: 128 threads per block,
+// 65536 registers per SM).
+#ifndef LTNE_ROWS_MINB2
+#define LTNE_ROWS_MINB2 4
+#endif
+#ifndef LTNE_ROWS_MINB4
+#define LTNE_ROWS_MINB4 2
+#endif
+
+template <typename S, int R>
+__global__ void __launch_bounds__(kPairMaxThreads, R == 2 ? LTNE_ROWS_MINB2 : LTNE_ROWS_MINB4)
+    k_step_pair_rows(
+    const S* __restrict__ src, S* __restrict__ dst, const float* __restrict__ phi_field,
+    float* __restrict__ mac, const NodeParams<F2> P, const NodeParams<float> P1, const int nx,
+    const int ny, const int64_t pitch, const int64_t plane, const float scale,
+    const float inv_scale, const int write_macros, const uint32_t* __restrict__ tick_in,
+    uint32_t* __restrict__ tick_out, const float* __restrict__ um_in, float* __restrict__ um_out) {
+  grid_dep_wait();
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  const uint32_t tick = read_tick<S, float>(tick_in, tick_out);
+  if (x0 >= nx || y0 >= ny) return;
+  const uint32_t pi = (uint32_t)pitch, pl = (uint32_t)plane;
+  if (!(x0 > 0 && x0 + 2 < nx)) {  // a side-wall pair or the odd last node: the plain code
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int y = y0 + k;
+      if (y >= ny) break;
+      if (x0 + 1 < nx) {
+        step_pair_side<S>(src, dst, phi_field, mac, P, x0, y, nx, ny, pi, pl, scale, inv_scale,
+                          write_macros, tick, um_in, um_out);
+      } else {
+        step_node<S, float, BC_CAVITY>(src, dst, phi_field, mac, P1, x0, y, nx, ny, pitch, plane,
+                                       scale, inv_scale, write_macros, tick, nullptr, um_in,
+                                       um_out);
+      }
+    }
+    return;
+  }
+  RawPair raw[2];
+  if (y0 > 0 && y0 < ny - 1) load_raw_pair<S>(src, pl, pi, x0, y0, raw[0]);
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int y = y0 + k;
+    if (y >= ny) break;
+    const int yn = y + 1;
+    if (k + 1 < R && yn < ny - 1) load_raw_pair<S>(src, pl, pi, x0, yn, raw[(k + 1) & 1]);
+    if (y > 0 && y < ny - 1) {
+      F2 f[9], gf[5], gs[5];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = dec_word<S>(raw[k & 1].w[i], inv_scale);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        gf[i] = dec_word<S>(raw[k & 1].w[9 + i], inv_scale);
+        gs[i] = dec_word<S>(raw[k & 1].w[14 + i], inv_scale);
+      }
+      finish_pair<S>(dst, phi_field, mac, P, (uint32_t)y * pi + (uint32_t)x0, pl, scale,
+                     write_macros, tick, um_in, um_out, f, gf, gs);
+    } else {  // the bottom or top wall row
+      step_pair<S, BC_CAVITY>(src, dst, phi_field, mac, P, x0, y, nx, ny, pi, pl, scale,
+                              inv_scale, write_macros, tick, um_in, um_out);
+    }
   }
 }
 
@@ -483,18 +560,27 @@ cudaError_t launch_step_pair_t(const LatticeArgs& a, const NodeParams<double>& P
   float* mac = static_cast<float*>(a.mac);
   const float* um_in = static_cast<const float*>(a.um_in);
   float* um_out = static_cast<float*>(a.um_out);
-  double* part = a.obs_part;
-  const float* prev = static_cast<const float*>(a.obs_prev);
   cudaError_t e;
+  if constexpr (sizeof(S) == 2) {
+    if (s.rows > 1 && a.bc == BC_CAVITY) {
+      const int R = s.rows >= 4 ? 4 : 2;
+      const dim3 rgrid(grid.x, (a.ny + s.by * R - 1) / (s.by * R));
+      if (R == 4)
+        e = launch_kernel(a.chained != 0, k_step_pair_rows<S, 4>, rgrid, block, 0, st, src, dst,
+                          phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,
+                          a.write_macros, a.tick_in, a.tick_out, um_in, um_out);
+      else
+        e = launch_kernel(a.chained != 0, k_step_pair_rows<S, 2>, rgrid, block, 0, st, src, dst,
+                          phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,
+                          a.write_macros, a.tick_in, a.tick_out, um_in, um_out);
+      if (e != cudaSuccess) return e;
+      return cudaGetLastError();
+    }
+  }
 #define LTNE_PAIR_LAUNCH(bc)                                                                   \
-  e = part ? launch_kernel(a.chained != 0, k_step_pair<S, bc, true>, grid, block, 0, st, src,  \
-                           dst, phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale,          \
-                           inv_scale, a.write_macros, a.tick_in, a.tick_out, um_in, um_out,    \
-                           part, prev)                                                         \
-           : launch_kernel(a.chained != 0, k_step_pair<S, bc, false>, grid, block, 0, st, src, \
-                           dst, phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale,          \
-                           inv_scale, a.write_macros, a.tick_in, a.tick_out, um_in, um_out,    \
-                           part, prev)
+  e = launch_kernel(a.chained != 0, k_step_pair<S, bc>, grid, block, 0, st, src, dst, phi,     \
+                    mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,                \
+                    a.write_macros, a.tick_in, a.tick_out, um_in, um_out)
   switch (a.bc) {
     case BC_CAVITY: LTNE_PAIR_LAUNCH(BC_CAVITY); break;
     case BC_PERIODIC: LTNE_PAIR_LAUNCH(BC_PERIODIC); break;

@@ -169,18 +169,4 @@ cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_partials(const double* partials, int64_t blocks, double* level,
-                                   double* out, cudaStream_t st) {
-  if (blocks <= kObsChunk) {
-    k_reduce_pass2<<<1, RB, 0, st>>>(partials, blocks, blocks, out);
-    return cudaGetLastError();
-  }
-  const int64_t g = (blocks + kObsChunk - 1) / kObsChunk;
-  k_reduce_pass2<<<(unsigned)g, RB, 0, st>>>(partials, blocks, kObsChunk, level);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_reduce_pass2<<<1, RB, 0, st>>>(level, g, g, out);
-  return cudaGetLastError();
-}
-
 }  // namespace ltne

@@ -1,13 +1,12 @@
 """The FP64 observables against an FP64 accumulation of the same FP32 fields.
 
-ltne_observables() combines block partials that the last step of an
-ltne_step() call accumulates while it writes the fields (two-part FP32 sums
-up to the warp, FP64 above); after set_fields or a checkpoint restore the
-stand-alone reduction pass does the same.  Here the fields the device holds
-are read back (exact in FP64) and the wall Nusselt numbers, mass, energy and
-residual are summed again in FP64 on the host: the device values must agree
-to a few FP64 rounding errors per sum, far below what plain FP32 partial
-sums would give at these sizes."""
+ltne_observables() reduces the fields of the current state: per-node terms
+summed as two-part FP32 values (error-free additions) up to the warp, FP64
+above.  Here the fields the device holds are read back (exact in FP64) and
+the wall Nusselt numbers, mass, energy and residual are summed again on the
+host with correctly rounded FP64 sums: the device values must agree to a few
+FP64 rounding errors per sum, far below what plain FP32 partial sums give at
+these sizes."""
 import numpy as np
 import pytest
 
@@ -68,9 +67,8 @@ def host_residual(a, b):
 def test_observables_agree_with_fp64_sums_of_the_same_fields(n, per_node):
     """8192 x 8192 (the reduced-storage configuration's physics, uniform
     porosity) and 2048 x 2048 (the throughput configuration's, porosity per
-    node), FP32 storage with the default schedules, from random fields: the
-    fused reduction after each ltne_step call, and the stand-alone pass on
-    the same state restored from a checkpoint."""
+    node), FP32 storage with the default schedules, from random fields; and
+    the same state restored from a checkpoint into a second handle."""
     if per_node:
         cfg = dict(W.C2_THROUGHPUT, nx=n, ny=n)
         phi = W.porosity_field(n, n, cfg["phi_lo"], cfg["phi_hi"], cfg["seed"])
