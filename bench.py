@@ -52,9 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096, help="cavity side (nodes)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
-    ap.add_argument("--npt", type=int, default=0, choices=[0, 1, 2, 4, 8],
-                    help="nodes per thread of the step kernel (0: the library default; 4, 8: "
-                         "a node pair in 2, 4 consecutive rows, 16-bit storage)")
+    ap.add_argument("--npt", type=int, default=0, choices=[0, 1, 2],
+                    help="nodes per thread of the step kernel (0: the library default)")
     ap.add_argument("--block", default="",
                     help="block shape bx,by of the step kernel (default: the library's)")
     ap.add_argument("--cavities", type=int, default=256,
@@ -70,6 +69,10 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the compact batched / adjoint / reduced-storage legs of the "
                          "default line")
+    ap.add_argument("--split", default="replicas", choices=["replicas", "slabs"],
+                    help="N > 1: replicas (one independent cavity per rank, weak scaling; "
+                         "default) or slabs (one cavity cut into N row slabs, halos exchanged "
+                         "with NCCL after every step, strong scaling)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: single cavity (default, the headline line); c3: 256-cavity "
                          "batch; c4: forward + adjoint; c5: reduced-storage forms at 8192^2 "
@@ -792,10 +795,86 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_slabs(args):
+    """The 4096 x 4096 cavity of the default line cut into one row slab per
+    rank (strong scaling): every step is followed by the halo exchange of
+    five populations per column and cut, through NCCL on the slab's stream;
+    the observables are the slabs' FP64 accumulators combined in rank
+    order.  Same timing rules as the default line (barrier, events on the
+    stream, max over ranks)."""
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local if ws > 1 else 0)
+    dist.init_process_group("nccl" if ws > 1 else "gloo", rank=rank, world_size=ws,
+                            **({} if ws > 1 else {"init_method": "tcp://127.0.0.1:%d"
+                                                  % _free_port()}))
+    from paper_1608_04118_gb300 import build as B
+
+    B.build()
+    from paper_1608_04118_gb300.ltne import LTNE_K_ERGUN, ltne_ergun_diameter
+    from paper_1608_04118_gb300.slabs import DistributedCavity
+
+    c = W.C2_THROUGHPUT
+    n = args.n
+    phi = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+    d = ltne_ergun_diameter(phi, n - 1, c["Da"])
+    kw = dict(Ra=c["Ra"], Pr=c["Pr"], Da=c["Da"], H=c["H"], gamma_sf=c["gamma_sf"],
+              sigma=c["sigma"], T_hot=c["T_hot"], T_cold=c["T_cold"], T_ref=c["T_ref"], d_p=d)
+    stream = torch.cuda.Stream()
+    dc = DistributedCavity(n, n, stream=stream, storage=args.storage, permeability=LTNE_K_ERGUN,
+                           porosity_field=1, **kw)
+    dc.set_fields(porosity=phi)
+    dc.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    dist.barrier()
+    l0 = dc.slab.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    dc.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = ev0.elapsed_time(ev1) / 1e3
+    t_max = max_over_ranks(t, torch.device("cuda", torch.cuda.current_device()))
+    ob = dc.observables()
+    # step kernels, plus the pack and unpack kernels of every step when the
+    # slab has a neighbour
+    launches = (dc.slab.launches - l0) * (3 if ws > 1 else 1)
+    if rank == 0:
+        value = n * n * args.steps / t_max / 1e6
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                "storage": args.storage, "data": "synthetic",
+                "config": dict(workload_config(n, args.storage),
+                               parallelism="row slabs x%d (one cavity, halo exchange per step)"
+                                           % ws),
+                "gpu_launches": int(launches),
+                "observables": {"Nu_f_hot": ob["Nu_f_hot"], "nonfinite": ob["nonfinite"],
+                                "step": ob["step"]}}
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _free_port():
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.split == "slabs":
+        run_slabs(args)
         return
     if args.workload == "c3":
         run_batch(args)

@@ -52,14 +52,12 @@ def tune_batch(batch, steps=8, warmup=2):
 
 
 # Single-lattice step kernel: block shapes (threads per block <= 256) and
-# nodes per thread (2 = paired FP32 arithmetic, not for FP64 storage; 4 and 8
-# = a node pair in 2 or 4 consecutive rows, 16-bit storage of a cavity).
+# nodes per thread (2 = paired FP32 arithmetic, not for FP64 storage).
 CAVITY_SHAPES = ((32, 2), (32, 4), (64, 1), (64, 2), (64, 4), (128, 1), (128, 2), (256, 1))
 
 
 def cavity_candidates(storage):
-    npts = (1,) if storage == "f64" else ((1, 2, 4, 8) if storage in ("f16", "bf16") else (1, 2))
-    for npt in npts:
+    for npt in ((1,) if storage == "f64" else (1, 2)):
         for bx, by in CAVITY_SHAPES:
             if npt == 1 or bx * by <= 128:  # the two-node kernels take <= 128 threads
                 yield bx, by, npt

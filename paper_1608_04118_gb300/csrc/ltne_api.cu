@@ -1054,20 +1054,13 @@ int ltne_set_schedule(ltne_handle* h, int32_t block_x, int32_t block_y,
   const int64_t threads = (int64_t)block_x * block_y;
   if (block_x < 32 || block_x > 256 || block_x % 32 != 0 || block_y < 1 || threads > 256)
     return LTNE_ERR_INVALID_ARG;
-  if (nodes_per_thread != 1 && nodes_per_thread != 2 && nodes_per_thread != 4 &&
-      nodes_per_thread != 8)
-    return LTNE_ERR_INVALID_ARG;
-  if (nodes_per_thread >= 2 &&
+  if (nodes_per_thread != 1 && nodes_per_thread != 2) return LTNE_ERR_INVALID_ARG;
+  if (nodes_per_thread == 2 &&
       (h->p.storage == LTNE_F64 || threads > kPairBlockThreads || h->slab))
-    return LTNE_ERR_INVALID_ARG;
-  // 4 / 8: a node pair in 2 / 4 consecutive rows (16-bit storage, cavity walls)
-  if (nodes_per_thread >= 4 && ((h->p.storage != LTNE_F16DEV && h->p.storage != LTNE_BF16DEV) ||
-                                h->p.bc != LTNE_BC_CAVITY))
     return LTNE_ERR_INVALID_ARG;
   h->shape.bx = block_x;
   h->shape.by = block_y;
-  h->shape.pair = nodes_per_thread >= 2 ? 1 : 0;
-  h->shape.rows = nodes_per_thread >= 4 ? nodes_per_thread / 2 : 1;
+  h->shape.pair = nodes_per_thread == 2 ? 1 : 0;
   drop_graphs(h);  // the captured launches carry the old configuration
   return LTNE_OK;
 }
@@ -1302,7 +1295,7 @@ int ltne_get_schedule(const ltne_handle* h, int32_t* block_x, int32_t* block_y,
   if (!h || !block_x || !block_y || !nodes_per_thread) return LTNE_ERR_INVALID_ARG;
   *block_x = h->shape.bx;
   *block_y = h->shape.by;
-  *nodes_per_thread = h->shape.pair ? 2 * h->shape.rows : 1;
+  *nodes_per_thread = h->shape.pair ? 2 : 1;
   return LTNE_OK;
 }
 

@@ -81,10 +81,7 @@ struct StepShape {
   int bx = 64;
   int by = 2;
   int pair = 0;
-  int tma = 0;   // two nodes per thread from TMA-staged tiles (cavity walls only)
-  int rows = 1;  // > 1: a pair of nodes in several consecutive rows per thread,
-                 // the next row's loads ahead of this row's arithmetic (16-bit
-                 // storage with cavity walls; the same bits as rows = 1)
+  int tma = 0;  // two nodes per thread from TMA-staged tiles (cavity walls only)
 };
 
 // Per-storage-type launchers (one translation unit each).

@@ -412,138 +412,6 @@ __global__ void __launch_bounds__(kPairMaxThreads, kPairMinBlocks) k_step_pair(
   }
 }
 
-// ---- 16-bit storage: one column pair over R consecutive rows ------------
-//
-// The two-node kernel above waits on its loads at 28 % warp occupancy (96
-// registers) and issues 58 % of the cycles.  Here a thread advances the
-// pair (x0, x0 + 1) in R consecutive rows and issues the 19 loads of row
-// y + 1 before the arithmetic of row y, so that one row's load latency is
-// covered by the previous row's work within the warp instead of by other
-// warps.  The loaded 16-bit values wait as 19 packed 32-bit words (even
-// node in the low half; the x-shifted pairs joined with one byte permute),
-// about 19 registers more than the plain form.  The arithmetic of a pair is
-// exactly that of the plain form (finish_pair), so both give the same bits.
-// Cavity walls only; wall rows and pairs holding a side-wall node take the
-// plain form's code.
-
-// The 19 values streaming into an interior pair, as packed 16-bit pairs.
-struct RawPair {
-  uint32_t w[19];
-};
-
-template <typename S>
-__device__ __forceinline__ void load_raw_pair(const S* __restrict__ src, uint32_t pl, uint32_t pi,
-                                              int x0, int y, RawPair& r) {
-  const uint16_t* __restrict__ s16 = reinterpret_cast<const uint16_t*>(src);
-  const uint32_t r0 = (uint32_t)y * pi, rm = r0 - pi, rp = r0 + pi;
-  const uint32_t a = (uint32_t)x0;
-  auto pair = [&](uint32_t k, uint32_t row) {
-    return *reinterpret_cast<const uint32_t*>(s16 + (k * pl + row + a));
-  };
-  auto left = [&](uint32_t k, uint32_t row) {  // columns x0 - 1, x0
-    const uint32_t q = k * pl + row + a;
-    return __byte_perm((uint32_t)s16[q - 1], (uint32_t)s16[q], 0x5410);
-  };
-  auto right = [&](uint32_t k, uint32_t row) {  // columns x0 + 1, x0 + 2
-    const uint32_t q = k * pl + row + a;
-    return __byte_perm((uint32_t)s16[q + 1], (uint32_t)s16[q + 2], 0x5410);
-  };
-  // the populations' source rows and columns as in PairPops::pull
-  r.w[0] = pair(0, r0);
-  r.w[1] = left(1, r0);
-  r.w[2] = pair(2, rm);
-  r.w[3] = right(3, r0);
-  r.w[4] = pair(4, rp);
-  r.w[5] = left(5, rm);
-  r.w[6] = right(6, rm);
-  r.w[7] = right(7, rp);
-  r.w[8] = left(8, rp);
-#pragma unroll
-  for (uint32_t t = 0; t < 2; ++t) {
-    const uint32_t k0 = t == 0 ? 9u : 14u;
-    r.w[k0] = pair(k0, r0);
-    r.w[k0 + 1] = left(k0 + 1, r0);
-    r.w[k0 + 2] = pair(k0 + 2, rm);
-    r.w[k0 + 3] = right(k0 + 3, r0);
-    r.w[k0 + 4] = pair(k0 + 4, rp);
-  }
-}
-
-template <typename S> __device__ __forceinline__ F2 dec_word(uint32_t w, float inv_scale);
-template <> __device__ __forceinline__ F2 dec_word<__half>(uint32_t w, float inv_scale) {
-  const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
-  return F2(mul2_(v, make_float2(inv_scale, inv_scale)));
-}
-template <> __device__ __forceinline__ F2 dec_word<__nv_bfloat16>(uint32_t w, float) {
-  return F2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
-
-// Resident blocks asked of the compiler for the row-pipelined form with 2
-// and with 4 rows per thread (the register budget: 128 threads per block,
-// 65536 registers per SM).
-#ifndef LTNE_ROWS_MINB2
-#define LTNE_ROWS_MINB2 4
-#endif
-#ifndef LTNE_ROWS_MINB4
-#define LTNE_ROWS_MINB4 2
-#endif
-
-template <typename S, int R>
-__global__ void __launch_bounds__(kPairMaxThreads, R == 2 ? LTNE_ROWS_MINB2 : LTNE_ROWS_MINB4)
-    k_step_pair_rows(
-    const S* __restrict__ src, S* __restrict__ dst, const float* __restrict__ phi_field,
-    float* __restrict__ mac, const NodeParams<F2> P, const NodeParams<float> P1, const int nx,
-    const int ny, const int64_t pitch, const int64_t plane, const float scale,
-    const float inv_scale, const int write_macros, const uint32_t* __restrict__ tick_in,
-    uint32_t* __restrict__ tick_out, const float* __restrict__ um_in, float* __restrict__ um_out) {
-  grid_dep_wait();
-  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  const uint32_t tick = read_tick<S, float>(tick_in, tick_out);
-  if (x0 >= nx || y0 >= ny) return;
-  const uint32_t pi = (uint32_t)pitch, pl = (uint32_t)plane;
-  if (!(x0 > 0 && x0 + 2 < nx)) {  // a side-wall pair or the odd last node: the plain code
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int y = y0 + k;
-      if (y >= ny) break;
-      if (x0 + 1 < nx) {
-        step_pair_side<S>(src, dst, phi_field, mac, P, x0, y, nx, ny, pi, pl, scale, inv_scale,
-                          write_macros, tick, um_in, um_out);
-      } else {
-        step_node<S, float, BC_CAVITY>(src, dst, phi_field, mac, P1, x0, y, nx, ny, pitch, plane,
-                                       scale, inv_scale, write_macros, tick, nullptr, um_in,
-                                       um_out);
-      }
-    }
-    return;
-  }
-  RawPair raw[2];
-  if (y0 > 0 && y0 < ny - 1) load_raw_pair<S>(src, pl, pi, x0, y0, raw[0]);
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int y = y0 + k;
-    if (y >= ny) break;
-    const int yn = y + 1;
-    if (k + 1 < R && yn < ny - 1) load_raw_pair<S>(src, pl, pi, x0, yn, raw[(k + 1) & 1]);
-    if (y > 0 && y < ny - 1) {
-      F2 f[9], gf[5], gs[5];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) f[i] = dec_word<S>(raw[k & 1].w[i], inv_scale);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        gf[i] = dec_word<S>(raw[k & 1].w[9 + i], inv_scale);
-        gs[i] = dec_word<S>(raw[k & 1].w[14 + i], inv_scale);
-      }
-      finish_pair<S>(dst, phi_field, mac, P, (uint32_t)y * pi + (uint32_t)x0, pl, scale,
-                     write_macros, tick, um_in, um_out, f, gf, gs);
-    } else {  // the bottom or top wall row
-      step_pair<S, BC_CAVITY>(src, dst, phi_field, mac, P, x0, y, nx, ny, pi, pl, scale,
-                              inv_scale, write_macros, tick, um_in, um_out);
-    }
-  }
-}
-
 template <typename S>
 cudaError_t launch_step_pair_t(const LatticeArgs& a, const NodeParams<double>& Pd, StepShape s,
                                cudaStream_t st) {
@@ -561,22 +429,6 @@ cudaError_t launch_step_pair_t(const LatticeArgs& a, const NodeParams<double>& P
   const float* um_in = static_cast<const float*>(a.um_in);
   float* um_out = static_cast<float*>(a.um_out);
   cudaError_t e;
-  if constexpr (sizeof(S) == 2) {
-    if (s.rows > 1 && a.bc == BC_CAVITY) {
-      const int R = s.rows >= 4 ? 4 : 2;
-      const dim3 rgrid(grid.x, (a.ny + s.by * R - 1) / (s.by * R));
-      if (R == 4)
-        e = launch_kernel(a.chained != 0, k_step_pair_rows<S, 4>, rgrid, block, 0, st, src, dst,
-                          phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,
-                          a.write_macros, a.tick_in, a.tick_out, um_in, um_out);
-      else
-        e = launch_kernel(a.chained != 0, k_step_pair_rows<S, 2>, rgrid, block, 0, st, src, dst,
-                          phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,
-                          a.write_macros, a.tick_in, a.tick_out, um_in, um_out);
-      if (e != cudaSuccess) return e;
-      return cudaGetLastError();
-    }
-  }
 #define LTNE_PAIR_LAUNCH(bc)                                                                   \
   e = launch_kernel(a.chained != 0, k_step_pair<S, bc>, grid, block, 0, st, src, dst, phi,     \
                     mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,                \

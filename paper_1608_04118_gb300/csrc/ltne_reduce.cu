@@ -5,30 +5,32 @@
 // Two passes with a fixed summation order, so results are bitwise
 // reproducible for a given lattice size: pass 1 writes one partial vector per
 // block (RB columns x seg rows) into a scratch buffer; pass 2 reduces the
-// partials in block order.  Per-node terms of FP32 fields are summed over at
-// most seg nodes per thread and across the 32 threads of a warp as two-part
-// FP32 sums (error-free additions, ltne_obs.cuh): FP64 on GB300 runs at a
-// small fraction of the FP32 rate, so FP64 per node -- or a warp shuffle
-// tree in FP64 in every block -- would make this pass compute-bound, while
-// the two-part sums carry about 48 significant bits at FP32 speed; every
-// combination above the warp, the warps of a block and the blocks, is FP64.
-// This pass serves the states whose last step did not accumulate the
-// observables itself (after set_fields, a checkpoint restore, the slab and
-// adjoint paths, the batched form and the allocation-free entry point).
-#include "ltne_obs.cuh"
+// partials in block order.  FP64 on GB300 runs at a small fraction of the
+// FP32 rate, so a thread of pass 1 sums its nodes' terms in the fields'
+// precision over its column segment (seg <= 64 rows) and only the threads'
+// sums are combined in FP64, through shared memory in a fixed order.  The
+// wall-flux integrals of Nu touch four columns only: pass 2 forms them in
+// FP64 from the first add while it combines the partials.  (Two-part FP32
+// sums with error-free additions for every term of every node made pass 1
+// bound by FP32 arithmetic, 0.32 ms at 4096^2.)
+#include "ltne_internal.h"
 
 namespace ltne {
 
 namespace {
 
 constexpr int RB = 256;  // threads per block in both passes
-// Rows per pass-1 block: the smallest of 16, 32, 64 that keeps the block
-// count within kReduceMaxBlocks (more, shorter blocks keep more loads in
-// flight: 2048^2 with 64 rows gives 256 blocks, fewer than two per SM).
+// Rows per pass-1 block: 64, 32 or 16, the longest that still gives 1024
+// blocks (enough resident warps to keep the loads of a memory-bound pass in
+// flight), within kReduceMaxBlocks.
 int reduce_seg(int nx, int ny) {
-  const int cols = (nx + RB - 1) / RB;
-  for (int seg = 16; seg < 64; seg *= 2)
-    if ((int64_t)cols * ((ny + seg - 1) / seg) <= kReduceMaxBlocks) return seg;
+  const int64_t cols = (nx + RB - 1) / RB;
+  for (int seg = 64; seg >= 16; seg /= 2) {
+    const int64_t b = cols * ((ny + seg - 1) / seg);
+    if (b >= 1024 && b <= kReduceMaxBlocks) return seg;
+  }
+  for (int seg = 16; seg <= 64; seg *= 2)
+    if (cols * ((ny + seg - 1) / seg) <= kReduceMaxBlocks) return seg;
   return 64;
 }
 
@@ -62,18 +64,22 @@ __device__ void block_reduce(double (&acc)[NACC], double* sh /* [RB/32][NACC] */
   }
 }
 
+static_assert(A_NUF_H == 0 && A_NUS_H == 1 && A_NUF_C == 2 && A_NUS_C == 3 && A_MASS == 4,
+              "the Nu slots come first");
+
 // Pass 1.  Block (RB threads) covers RB consecutive columns and seg rows;
 // each thread walks its column down the segment (coalesced rows across the
-// warp) and accumulates its nodes' terms (obs_node) as two-part FP32 sums,
-// then the warp, then the warps' partials in FP64 (obs_block_store).  Rows
-// go in groups of RU (4 in FP32, 2 in FP64, which holds twice the
-// registers per value): all loads of a group are issued before any of its
-// snapshot stores, so a thread keeps RU rows of loads in flight.
+// warp).  Rows go in groups of RU (4 in FP32, 2 in FP64, which holds twice
+// the registers per value): all loads of a group are issued before any of
+// its snapshot stores, so a thread keeps RU rows of loads in flight.
 template <typename C>
 __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
   constexpr int RU = sizeof(C) == 4 ? 4 : 2;
-  ObsAcc<C> acc;
-  obs_zero(acc);
+  __shared__ double sh[NACC][RB];
+  const int t = threadIdx.x;
+  C acc[NACC];  // the thread's sums (slots from A_MASS on)
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k] = C(0);
   const C* __restrict__ mac = static_cast<const C*>(a.mac);
   const C* __restrict__ phi_f = static_cast<const C*>(a.phi);
   C* __restrict__ prev = static_cast<C*>(a.prev);
@@ -83,6 +89,7 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
   const int y1 = min(y0 + seg, a.ny);
   const C phi_u = C(a.phi_u), sigma = C(a.sigma);
   if (x < a.nx) {
+#pragma unroll 1
     for (int yg = y0; yg < y1; yg += RU) {
       // deviations: rho - 1, ux, uy, T_f - T0, T_s - T0; the previous
       // snapshot of ux, uy, T_f, T_s
@@ -106,9 +113,26 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
       for (int r = 0; r < RU; ++r) {
         const int y = yg + r;
         if (y >= y1) break;
-        const C wy = ((y == 0 && a.wall_lo) || (y == a.ny - 1 && a.wall_hi)) ? C(0.5) : C(1);
-        obs_node<C>(acc, rho[r], ux[r], uy[r], Tf[r], Ts[r], phi[r], sigma, pux[r], puy[r],
-                    pTf[r], pTs[r], wy, x, a.nx);
+        acc[A_MASS] += rho[r];
+        // deviation part of phi T_f + (1-phi) sigma T_s; the T0 and Q parts
+        // are restored from the porosity sum in FP64
+        acc[A_ENERGY] += phi[r] * Tf[r] + (C(1) - phi[r]) * sigma * Ts[r];
+        acc[A_SUMPHI] += phi[r];
+        const C u2 = ux[r] * ux[r] + uy[r] * uy[r];
+        acc[A_MAXU] = u2 > acc[A_MAXU] ? u2 : acc[A_MAXU];  // |u|^2, rooted in FP64
+        const C dT = Tf[r] > Ts[r] ? Tf[r] - Ts[r] : Ts[r] - Tf[r];
+        acc[A_MAXDT] = dT > acc[A_MAXDT] ? dT : acc[A_MAXDT];
+        acc[A_SUMTF] += Tf[r];
+        acc[A_SUMTS] += Ts[r];
+        acc[A_DU2] += (ux[r] - pux[r]) * (ux[r] - pux[r]) + (uy[r] - puy[r]) * (uy[r] - puy[r]);
+        acc[A_U2] += u2;
+        acc[A_DTF2] += (Tf[r] - pTf[r]) * (Tf[r] - pTf[r]);
+        acc[A_TF2] += Tf[r] * Tf[r];
+        acc[A_DTS2] += (Ts[r] - pTs[r]) * (Ts[r] - pTs[r]);
+        acc[A_TS2] += Ts[r] * Ts[r];
+        if (!(isfinite(rho[r]) && isfinite(ux[r]) && isfinite(uy[r]) && isfinite(Tf[r]) &&
+              isfinite(Ts[r])))
+          acc[A_BAD] += C(1);
       }
       if (a.update_prev) {
 #pragma unroll
@@ -124,28 +148,58 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
       }
     }
   }
-  obs_block_store<C>(acc, a.partials);
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) sh[k][t] = (double)acc[k];  // the Nu slots stay 0
+  // the block's threads in FP64, in a fixed order: eight column chunks of
+  // 32 threads per accumulator, then the chunks
+  __syncthreads();
+  __shared__ double sh2[NACC][RB / 32];
+  if (threadIdx.x < NACC * (RB / 32)) {
+    const int k = threadIdx.x / (RB / 32), c = threadIdx.x % (RB / 32);
+    double v = sh[k][c * 32];
+    for (int i = 1; i < 32; ++i) v = combine<double>(k, v, sh[k][c * 32 + i]);
+    sh2[k][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NACC) {
+    const int k = threadIdx.x;
+    double v = sh2[k][0];
+    for (int c = 1; c < RB / 32; ++c) v = combine<double>(k, v, sh2[k][c]);
+    const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    a.partials[b * NACC + k] = v;
+  }
 }
 
-// Block b combines partial vectors [b * chunk, min((b + 1) * chunk, blocks))
-// into out[b] (fixed order: thread strides, then the block tree).
-__global__ void __launch_bounds__(RB) k_reduce_pass2(const double* __restrict__ partials,
-                                                     int64_t blocks, int64_t chunk,
-                                                     double* __restrict__ out) {
+// Pass 2 (one block): the partial vectors in block order, and the wall-flux
+// integrals of Nu in FP64 -- q_hot = 1.5 T_h - 2 T(1,y) + 0.5 T(2,y) and
+// q_cold = -1.5 T_c + 2 T(nx-2,y) - 0.5 T(nx-3,y) of both phases (their
+// deviation parts; the wall terms are added on the host), trapezoid rule in
+// y -- thread t taking rows t, t + RB, ...; then the block tree.
+template <typename C>
+__global__ void __launch_bounds__(RB) k_reduce_pass2(ReduceArgs a) {
   __shared__ double sh[(RB / 32) * NACC];
   double acc[NACC];
 #pragma unroll
   for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
-  const int64_t b0 = (int64_t)blockIdx.x * chunk;
-  const int64_t b1 = b0 + chunk < blocks ? b0 + chunk : blocks;
-  for (int64_t b = b0 + threadIdx.x; b < b1; b += RB)
+  for (int b = threadIdx.x; b < a.blocks; b += RB)
 #pragma unroll
-    for (int k = 0; k < NACC; ++k)
-      acc[k] = combine<double>(k, acc[k], partials[b * NACC + k]);
+    for (int k = A_MASS; k < NACC; ++k)
+      acc[k] = combine<double>(k, acc[k], a.partials[(int64_t)b * NACC + k]);
+  const C* __restrict__ mac = static_cast<const C*>(a.mac);
+  const int64_t pl = a.plane;
+  for (int y = threadIdx.x; y < a.ny; y += RB) {
+    const double wy = ((y == 0 && a.wall_lo) || (y == a.ny - 1 && a.wall_hi)) ? 0.5 : 1.0;
+    const C* tf = mac + 3 * pl + (int64_t)y * a.pitch;
+    const C* ts = tf + pl;
+    acc[A_NUF_H] += wy * (-2.0 * (double)tf[1] + 0.5 * (double)tf[2]);
+    acc[A_NUS_H] += wy * (-2.0 * (double)ts[1] + 0.5 * (double)ts[2]);
+    acc[A_NUF_C] += wy * (2.0 * (double)tf[a.nx - 2] - 0.5 * (double)tf[a.nx - 3]);
+    acc[A_NUS_C] += wy * (2.0 * (double)ts[a.nx - 2] - 0.5 * (double)ts[a.nx - 3]);
+  }
   block_reduce(acc, sh);
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) out[(int64_t)blockIdx.x * NACC + k] = acc[k];
+    for (int k = 0; k < NACC; ++k) a.out[k] = acc[k];
 }
 
 }  // namespace
@@ -165,7 +219,10 @@ cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
     k_reduce_pass1<float><<<grid, RB, 0, st>>>(a, seg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_reduce_pass2<<<1, RB, 0, st>>>(a.partials, a.blocks, a.blocks, a.out);
+  if (a.is_double)
+    k_reduce_pass2<double><<<1, RB, 0, st>>>(a);
+  else
+    k_reduce_pass2<float><<<1, RB, 0, st>>>(a);
   return cudaGetLastError();
 }
 

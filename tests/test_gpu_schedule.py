@@ -95,30 +95,12 @@ def test_block_shape_changes_no_bit(storage, npt):
             assert np.array_equal(f[k], ref[k]), (shape, k)
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
-def test_row_pipelined_form_gives_the_pair_bits(storage):
-    """The 16-bit form that advances a node pair over 2 or 4 consecutive rows
-    (the next row's loads ahead of this row's arithmetic) gives the bits of
-    the two-node form: ragged width and height, both walls, per-node
-    porosity."""
-    nx, ny = 203, 77
-    cfg = W.random_params(33, nx, ny)
-    phi = W.porosity_field(nx, ny, 0.3, 0.9, seed=34).reshape(-1)
-    ref = _run(cfg, 150, storage, (32, 4, 2), phi=phi).fields()
-    for sch in ((32, 4, 4), (32, 4, 8), (64, 2, 8), (32, 1, 4), (128, 1, 8)):
-        c = _run(cfg, 150, storage, sch, phi=phi)
-        assert c.schedule == sch
-        f = c.fields()
-        for k in f:
-            assert np.array_equal(f[k], ref[k]), (sch, k)
-
-
 RED = pytest.mark.xfail(strict=True, reason="BF16 deviations from the rest equilibrium cannot "
                         "reach 1e-3 in u: one stochastic rounding of the exact state already "
                         "puts 1.2e-3 into j/rho")
 
 
-@pytest.mark.parametrize("schedule", [(128, 2, 1), (32, 4, 2), (32, 4, 8)])
+@pytest.mark.parametrize("schedule", [(128, 2, 1), (32, 4, 2)])
 @pytest.mark.parametrize("storage", ["f16", pytest.param("bf16", marks=RED)])
 def test_reduced_storage_both_forms_64_cavity(storage, schedule):
     """The forms of the 16-bit kernels on the 64 x 64 cavity after 10^4
