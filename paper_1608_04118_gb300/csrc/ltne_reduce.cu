@@ -20,14 +20,15 @@ namespace ltne {
 namespace {
 
 constexpr int RB = 256;  // threads per block in both passes
-// Rows per pass-1 block: 64, 32 or 16, the longest that still gives 1024
-// blocks (enough resident warps to keep the loads of a memory-bound pass in
-// flight), within kReduceMaxBlocks.
+// Rows per pass-1 block: 64, 32 or 16, the longest that still gives 2048
+// blocks (about three waves of the 4-5 blocks an SM holds: enough resident
+// warps to keep the loads in flight, and a short last wave), within
+// kReduceMaxBlocks.  (1024 blocks of 64 rows at 4096^2: 0.22 ms per call.)
 int reduce_seg(int nx, int ny) {
   const int64_t cols = (nx + RB - 1) / RB;
   for (int seg = 64; seg >= 16; seg /= 2) {
     const int64_t b = cols * ((ny + seg - 1) / seg);
-    if (b >= 1024 && b <= kReduceMaxBlocks) return seg;
+    if (b >= 2048 && b <= kReduceMaxBlocks) return seg;
   }
   for (int seg = 16; seg <= 64; seg *= 2)
     if (cols * ((ny + seg - 1) / seg) <= kReduceMaxBlocks) return seg;
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(RB) k_reduce_pass2(ReduceArgs a) {
       acc[k] = combine<double>(k, acc[k], a.partials[(int64_t)b * NACC + k]);
   const C* __restrict__ mac = static_cast<const C*>(a.mac);
   const int64_t pl = a.plane;
+#pragma unroll 4
   for (int y = threadIdx.x; y < a.ny; y += RB) {
     const double wy = ((y == 0 && a.wall_lo) || (y == a.ny - 1 && a.wall_hi)) ? 0.5 : 1.0;
     const C* tf = mac + 3 * pl + (int64_t)y * a.pitch;
