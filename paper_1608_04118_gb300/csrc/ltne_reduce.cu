@@ -166,42 +166,46 @@ __global__ void __launch_bounds__(RB) k_reduce_pass1(ReduceArgs a, int seg) {
     const int k = threadIdx.x;
     double v = sh2[k][0];
     for (int c = 1; c < RB / 32; ++c) v = combine<double>(k, v, sh2[k][c]);
+    // accumulator-major: pass 2 reads each accumulator's partials contiguously
     const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    a.partials[b * NACC + k] = v;
+    a.partials[(int64_t)k * a.blocks + b] = v;
   }
 }
 
-// Pass 2 (one block): the partial vectors in block order, and the wall-flux
-// integrals of Nu in FP64 -- q_hot = 1.5 T_h - 2 T(1,y) + 0.5 T(2,y) and
-// q_cold = -1.5 T_c + 2 T(nx-2,y) - 0.5 T(nx-3,y) of both phases (their
+// Pass 2: block k forms accumulator k -- the partials of pass 1 in block
+// order (contiguous, accumulator-major), or for the four Nu slots the
+// wall-flux integral in FP64: q_hot = 1.5 T_h - 2 T(1,y) + 0.5 T(2,y) and
+// q_cold = -1.5 T_c + 2 T(nx-2,y) - 0.5 T(nx-3,y) of one phase (their
 // deviation parts; the wall terms are added on the host), trapezoid rule in
-// y -- thread t taking rows t, t + RB, ...; then the block tree.
+// y -- thread t taking rows or partials t, t + RB, ..., then the block tree.
 template <typename C>
 __global__ void __launch_bounds__(RB) k_reduce_pass2(ReduceArgs a) {
   __shared__ double sh[(RB / 32) * NACC];
   double acc[NACC];
 #pragma unroll
   for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < a.blocks; b += RB)
-#pragma unroll
-    for (int k = A_MASS; k < NACC; ++k)
-      acc[k] = combine<double>(k, acc[k], a.partials[(int64_t)b * NACC + k]);
-  const C* __restrict__ mac = static_cast<const C*>(a.mac);
-  const int64_t pl = a.plane;
+  const int k = blockIdx.x;
+  double v = 0.0;
+  if (k >= A_MASS) {
+    const double* __restrict__ p = a.partials + (int64_t)k * a.blocks;
 #pragma unroll 4
-  for (int y = threadIdx.x; y < a.ny; y += RB) {
-    const double wy = ((y == 0 && a.wall_lo) || (y == a.ny - 1 && a.wall_hi)) ? 0.5 : 1.0;
-    const C* tf = mac + 3 * pl + (int64_t)y * a.pitch;
-    const C* ts = tf + pl;
-    acc[A_NUF_H] += wy * (-2.0 * (double)tf[1] + 0.5 * (double)tf[2]);
-    acc[A_NUS_H] += wy * (-2.0 * (double)ts[1] + 0.5 * (double)ts[2]);
-    acc[A_NUF_C] += wy * (2.0 * (double)tf[a.nx - 2] - 0.5 * (double)tf[a.nx - 3]);
-    acc[A_NUS_C] += wy * (2.0 * (double)ts[a.nx - 2] - 0.5 * (double)ts[a.nx - 3]);
+    for (int b = threadIdx.x; b < a.blocks; b += RB) v = combine<double>(k, v, p[b]);
+  } else {
+    const C* __restrict__ mac = static_cast<const C*>(a.mac);
+    const C* __restrict__ T = mac + (k == A_NUF_H || k == A_NUF_C ? 3 : 4) * a.plane;
+    const bool hot = k == A_NUF_H || k == A_NUS_H;
+    const int c1 = hot ? 1 : a.nx - 2, c2 = hot ? 2 : a.nx - 3;
+    const double w1 = hot ? -2.0 : 2.0, w2 = hot ? 0.5 : -0.5;
+#pragma unroll 4
+    for (int y = threadIdx.x; y < a.ny; y += RB) {
+      const double wy = ((y == 0 && a.wall_lo) || (y == a.ny - 1 && a.wall_hi)) ? 0.5 : 1.0;
+      const C* row = T + (int64_t)y * a.pitch;
+      v += wy * (w1 * (double)row[c1] + w2 * (double)row[c2]);
+    }
   }
+  acc[k] = v;
   block_reduce(acc, sh);
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < NACC; ++k) a.out[k] = acc[k];
+  if (threadIdx.x == 0) a.out[k] = acc[k];
 }
 
 }  // namespace
@@ -222,9 +226,9 @@ cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.is_double)
-    k_reduce_pass2<double><<<1, RB, 0, st>>>(a);
+    k_reduce_pass2<double><<<NACC, RB, 0, st>>>(a);
   else
-    k_reduce_pass2<float><<<1, RB, 0, st>>>(a);
+    k_reduce_pass2<float><<<NACC, RB, 0, st>>>(a);
   return cudaGetLastError();
 }
 
