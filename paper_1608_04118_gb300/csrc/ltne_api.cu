@@ -602,12 +602,21 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   if (rc != LTNE_OK) return rc;
   drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
 
-  // Zero the whole workspace first -- population buffers, porosity,
-  // macroscopic fields, residual snapshot, |u| planes, counters -- so that
-  // row and plane padding, which no kernel writes, is zero and state blobs
-  // are deterministic.
+  // Zero the whole workspace first -- population buffers, porosity, both
+  // macro sets, |u| planes, counters -- so that row and plane padding, which
+  // no kernel writes, is zero and state blobs are deterministic.  A lattice
+  // without padding (nx a multiple of 64, nx * ny of 128) has none: every
+  // element of the other planes is written before it is read, and only the
+  // macro set the fields are staged into must start at zero (a field not
+  // given is a zero deviation).  At 4096^2 that is 0.34 GB instead of 3 GB.
   {
-    const cudaError_t ez = cudaMemsetAsync(h->ws, 0, h->ws_bytes, h->stream);
+    // (a slab's halo rows keep planes no step writes: always zeroed)
+    const bool padded =
+        h->slab || h->pitch != p.nx || h->plane != h->pitch * (int64_t)p.ny;
+    const cudaError_t ez =
+        padded ? cudaMemsetAsync(h->ws, 0, h->ws_bytes, h->stream)
+               : cudaMemsetAsync(h->ws + h->off_mac[0], 0, 5 * (size_t)h->plane * h->ec,
+                                 h->stream);
     if (ez != cudaSuccess) return fail_cuda(ez);
   }
 
