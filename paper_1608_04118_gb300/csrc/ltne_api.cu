@@ -466,12 +466,6 @@ void layout(ltne_handle* h) {
   off = align_up(off + (size_t)h->red_blocks * NACC * sizeof(double), A);
   h->off_out = off;
   off = align_up(off + NACC * sizeof(double), A);
-  // the observables' block partials of the last step of a call: room for
-  // the grids of the default launch shapes (one node per thread in 64 x 2
-  // blocks; two in 128 x 1 or 32 x 4)
-  h->fpart_cap = (int64_t)((p.nx + 63) / 64) * ((p.ny + 1) / 2);
-  h->off_fpart = off;
-  off = align_up(off + (size_t)h->fpart_cap * NACC * sizeof(double), A);
   h->off_tick = off;  // two uint32 step counters for the stochastic rounding, then
   off = align_up(off + 3 * sizeof(uint32_t), A);  // the device error word
   for (int b = 0; b < 2; ++b) {  // |u| of the previous state per buffer (Eq. 52)
@@ -524,19 +518,8 @@ cudaError_t launch_step(ltne_handle* h, int src_buf, int write_macros, cudaStrea
 }
 
 // Point the current macro set at the one the next write of the fields
-// goes to (never the residual snapshot); the block partials of an earlier
-// step no longer describe the fields.
-void begin_macro_write(ltne_handle* h) {
-  h->mcur = mac_next(h);
-  h->fused_valid = false;
-}
-
-// Blocks of the step grid for the handle's launch shape.
-int64_t step_blocks(const ltne_handle* h) {
-  const int64_t cols = h->shape.pair ? (h->p.nx + 1) / 2 : h->p.nx;
-  return ((cols + h->shape.bx - 1) / h->shape.bx) *
-         (((int64_t)h->p.ny + h->shape.by - 1) / h->shape.by);
-}
+// goes to (never the residual snapshot).
+void begin_macro_write(ltne_handle* h) { h->mcur = mac_next(h); }
 
 void drop_graphs(ltne_handle* h) {
   for (auto& g : h->graph)
@@ -650,7 +633,6 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   };
   h->mcur = 0;  // the fields go to macro set 0; no residual snapshot yet
   h->msnap = -1;
-  h->fused_valid = false;
   for (int k = 0; k < 5; ++k) {
     if (!src[k]) continue;
     rc = stage(src[k], defaults[k], refs[k], mac_cur(h) + (size_t)k * h->plane * h->ec);
@@ -721,10 +703,7 @@ int reduce_handle(ltne_handle* h, double* acc) {
   cudaError_t e = cudaMemcpyAsync(acc, h->ws + h->off_out, NACC * sizeof(double),
                                   cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess) {  // these fields are the next residual's reference
-    h->msnap = h->mcur;
-    h->fused_valid = false;
-  }
+  if (e == cudaSuccess) h->msnap = h->mcur;  // these fields are the next residual's reference
   return fail_cuda(e);
 }
 
@@ -909,28 +888,9 @@ int ltne_step(ltne_handle* h, int64_t n) {
     ++h->step;
     ++h->launches;
   }
-  // the last step writes the fields and, unless its grid outgrows the
-  // partials' room or the tiles are staged, the observables' block partials
-  // against the residual reference
-  begin_macro_write(h);
-  LatticeArgs a = lattice_args(h, h->cur, 1);
-  a.chained = chained ? 1 : 0;
-  const int64_t blocks = step_blocks(h);
-  const bool fuse = !h->shape.tma && blocks <= h->fpart_cap;
-  if (fuse) {
-    a.obs_part = reinterpret_cast<double*>(h->ws + h->off_fpart);
-    a.obs_prev = h->msnap >= 0 ? h->ws + h->off_mac[h->msnap] + (size_t)h->plane * h->ec
-                               : nullptr;
-  }
-  switch (h->p.storage) {
-    case LTNE_F64: e = launch_step_f64(a, h->P, h->shape, h->stream); break;
-    case LTNE_F32: e = launch_step_f32(a, h->P, h->shape, h->stream); break;
-    case LTNE_F16DEV: e = launch_step_f16(a, h->P, h->shape, h->stream); break;
-    default: e = launch_step_bf16(a, h->P, h->shape, h->stream); break;
-  }
+  begin_macro_write(h);  // the last step writes the fields
+  e = launch_step(h, h->cur, 1, h->stream, chained);
   if (e != cudaSuccess) return fail_cuda(e);
-  h->fused_valid = fuse;
-  h->fused_blocks = blocks;
   h->cur ^= 1;
   ++h->step;
   ++h->launches;
@@ -950,23 +910,8 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
       return fail_cuda(e);
     }
   }
-  if (h->fused_valid) {  // the last step left the block partials: combine them
-    ReduceArgs a;
-    a.mac = mac_cur(h);
-    a.partials = reinterpret_cast<double*>(h->ws + h->off_fpart);
-    a.out = reinterpret_cast<double*>(h->ws + h->off_out);
-    a.nx = p.nx;
-    a.ny = p.ny;
-    a.pitch = h->pitch;
-    a.plane = h->plane;
-    a.blocks = (int)h->fused_blocks;
-    a.is_double = h->ec == 8;
-    e = launch_reduce_pass2(a, h->stream);
-    if (e != cudaSuccess) return fail_cuda(e);
-  } else {
-    const int rr = reduce_launch(h);
-    if (rr != LTNE_OK) return rr;
-  }
+  const int rr = reduce_launch(h);
+  if (rr != LTNE_OK) return rr;
   // the accumulators and the device error word in one read-back: a staged
   // step that gave up waiting for its tile reports here (the fields are then
   // not trustworthy); the word is cleared
@@ -992,7 +937,6 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   const int rc = finish_observables(p, info, h->step, h->msnap >= 0, acc, out);
   h->have_prev = true;
   h->msnap = h->mcur;  // these fields are the next residual's reference
-  h->fused_valid = false;
   return rc;
 }
 
@@ -1074,7 +1018,6 @@ int ltne_set_state(ltne_handle* h, const void* host, size_t bytes) {
   const size_t pb = 19 * (size_t)h->plane * h->es, mb = 5 * (size_t)h->plane * h->ec;
   h->mcur = 0;  // the restored fields in macro set 0; no residual snapshot
   h->msnap = -1;
-  h->fused_valid = false;
   cudaError_t e = cudaMemcpyAsync(h->ws + h->off_pop[0], src, pb, cudaMemcpyHostToDevice,
                                   h->stream);
   if (e == cudaSuccess)

@@ -22,10 +22,6 @@ struct ltne_handle {
   // two sets of the 5 macro planes: the current state's, and the snapshot
   // taken by the last ltne_observables call (the residual's reference)
   size_t off_mac[2] = {0, 0};
-  // the observables' block partials left by the last step of an ltne_step
-  // call (accumulator-major), with room for fpart_cap blocks
-  size_t off_fpart = 0;
-  int64_t fpart_cap = 0;
   size_t off_tick = 0;
   size_t off_um[2] = {0, 0};  // |u| planes (local h_v of Eq. 52)
   size_t ws_bytes = 0;
@@ -38,8 +34,6 @@ struct ltne_handle {
   bool have_prev = false;
   int mcur = 0;             // macro set holding the current state's fields
   int msnap = -1;           // macro set holding the snapshot (-1: none yet)
-  bool fused_valid = false; // the block partials describe the current fields
-  int64_t fused_blocks = 0; // and this many blocks wrote them
   float enc_scale = 1.0f;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t launches = 0;

@@ -40,14 +40,6 @@ struct LatticeArgs {
   int* err;                 // device error word: set by a bounded wait that gave up
   int slab_walls;           // BC_SLAB: which of the first / last rows are walls
   int chained;              // launch as a programmatic dependent of the stream's last kernel
-  // The observables' block partials accumulated by this step (the last of
-  // an ltne_step call; write_macros = 1): obs_part receives, accumulator-
-  // major (slot k of block b at k * blocks + b), the slots from A_MASS on;
-  // obs_prev points at the residual reference's u_x plane (u_x, u_y,
-  // T_f - T0, T_s - T0 at plane stride), or is null for none (differences
-  // 0).  obs_part null: a plain step.
-  double* obs_part;
-  const void* obs_prev;
 };
 
 // Programmatic dependent launch.  A kernel launched with programmatic
@@ -129,9 +121,6 @@ struct ReduceArgs {
 };
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
-// Pass 2 alone: a.partials holds a.blocks accumulator-major partial vectors
-// (slots from A_MASS on); the Nu slots come from the fields at a.mac.
-cudaError_t launch_reduce_pass2(const ReduceArgs& a, cudaStream_t st);
 
 // Halo rows of a row slab (ltne_slab.cu).  Pack: the populations of the
 // slab's first computed row that stream down (e_y = -1: f_4, f_7, f_8,

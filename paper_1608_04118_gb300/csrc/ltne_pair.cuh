@@ -220,16 +220,10 @@ __device__ __forceinline__ void st_f2(float* __restrict__ p, F2 v) {
   *reinterpret_cast<float2*>(p) = v.v;
 }
 
-// The observables' accumulation of a pair (the last step of a call).
-struct PairObs {
-  FuseAcc<float>* acc;
-  const float* prev;  // the residual reference's u_x plane, or null
-};
-
 // Everything after the pull for a pair at element offset off whose
 // pre-collision values are in f, gf, gs: macroscopic values, collision,
 // stores.  Shared by the pull from HBM and the pull from a staged tile.
-template <typename S, bool OBS = false>
+template <typename S>
 __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
                                             const float* __restrict__ phi_field,
                                             float* __restrict__ mac, const NodeParams<F2>& P,
@@ -237,7 +231,7 @@ __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
                                             const float scale, const int write_macros,
                                             const uint32_t tick, const float* __restrict__ um_in,
                                             float* __restrict__ um_out, F2 (&f)[9], F2 (&gf)[5],
-                                            F2 (&gs)[5], const PairObs* ob = nullptr) {
+                                            F2 (&gs)[5]) {
   Medium<F2> md = phi_field ? medium_at<F2>(P, ld_f2(phi_field + off)) : P.um;
   if (P.hv_local) set_exchange<F2>(md, hv_local_at<F2>(P, ld_f2(um_in + off)));
   Macro<F2> m;
@@ -250,19 +244,6 @@ __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
     st_f2(mac + 3u * pl + off, m.dTf);
     st_f2(mac + 4u * pl + off, m.dTs);
   }
-  if constexpr (OBS) {
-    F2 pux = m.ux, puy = m.uy, pTf = m.dTf, pTs = m.dTs;
-    if (ob->prev) {
-      pux = ld_f2(ob->prev + off);
-      puy = ld_f2(ob->prev + pl + off);
-      pTf = ld_f2(ob->prev + 2u * pl + off);
-      pTs = ld_f2(ob->prev + 3u * pl + off);
-    }
-    fuse_node<float>(*ob->acc, m.drho.v.x, m.ux.v.x, m.uy.v.x, m.dTf.v.x, m.dTs.v.x, md.phi.v.x,
-                     P.sigma.v.x, pux.v.x, puy.v.x, pTf.v.x, pTs.v.x);
-    fuse_node<float>(*ob->acc, m.drho.v.y, m.ux.v.y, m.uy.v.y, m.dTf.v.y, m.dTs.v.y, md.phi.v.y,
-                     P.sigma.v.y, pux.v.y, puy.v.y, pTf.v.y, pTs.v.y);
-  }
   collide<F2>(P, m, f, gf, gs);
   PairPops<S>::store(dst, pl, off, scale, f, gf, gs, off, tick);
 }
@@ -270,7 +251,7 @@ __device__ __forceinline__ void finish_pair(S* __restrict__ dst,
 // The pair (x0, y), (x0 + 1, y) when both nodes exist and neither is a
 // left/right wall node: interior nodes, or both on a no-slip adiabatic row
 // (same rebuild, from the row above or below).
-template <typename S, int BC, bool OBS = false>
+template <typename S, int BC>
 __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restrict__ dst,
                                           const float* __restrict__ phi_field,
                                           float* __restrict__ mac, const NodeParams<F2>& P,
@@ -278,8 +259,7 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
                                           const uint32_t pi, const uint32_t pl, const float scale,
                                           const float inv_scale, const int write_macros,
                                           const uint32_t tick, const float* __restrict__ um_in,
-                                          float* __restrict__ um_out,
-                                          const PairObs* ob = nullptr) {
+                                          float* __restrict__ um_out) {
   int cy = y;
   bool wall_row = false;
   if (BC == BC_CAVITY || BC == BC_CHANNEL) {
@@ -309,8 +289,8 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
     macros<F2>(P, mdn, f, gf, gs, mn);
     nee<F2>(P, mn, mn.dTf, mn.dTs, f, gf, gs);  // adiabatic: the neighbour's temperatures
   }
-  finish_pair<S, OBS>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out,
-                      f, gf, gs, ob);
+  finish_pair<S>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out, f, gf,
+                 gs);
 }
 
 // A cavity pair holding a left or right wall node (x0 = 0, or x0 + 1 =
@@ -323,7 +303,7 @@ __device__ __forceinline__ void step_pair(const S* __restrict__ src, S* __restri
 // lanes continue as any pair.  The same rebuild as the one-node step, in
 // paired arithmetic, without the warp divergence of two one-node steps
 // beside the pairs of the rest of the row.
-template <typename S, bool OBS = false>
+template <typename S>
 __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __restrict__ dst,
                                                const float* __restrict__ phi_field,
                                                float* __restrict__ mac, const NodeParams<F2>& P,
@@ -332,8 +312,7 @@ __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __r
                                                const float scale, const float inv_scale,
                                                const int write_macros, const uint32_t tick,
                                                const float* __restrict__ um_in,
-                                               float* __restrict__ um_out,
-                                               const PairObs* ob = nullptr) {
+                                               float* __restrict__ um_out) {
   const bool left = x0 == 0;
   const bool wall_row = y == 0 || y == ny - 1;
   const int cx = left ? 1 : nx - 2;
@@ -391,8 +370,8 @@ __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __r
     gs[i] = pick(rgs[i], gs[i]);
   }
   const uint32_t off = (uint32_t)y * pi + (uint32_t)x0;
-  finish_pair<S, OBS>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out,
-                      f, gf, gs, ob);
+  finish_pair<S>(dst, phi_field, mac, P, off, pl, scale, write_macros, tick, um_in, um_out, f, gf,
+                 gs);
 }
 
 // Register budget of the pair kernel: blocks of at most 128 threads and at
@@ -404,49 +383,17 @@ __device__ __forceinline__ void step_pair_side(const S* __restrict__ src, S* __r
 constexpr int kPairMaxThreads = kPairBlockThreads;
 constexpr int kPairMinBlocks = 5;
 
-// OBS: the last step of an ltne_step call, which also leaves the
-// observables' block partials (its own instantiation, once per call, with
-// a looser register budget than the plain form's).
-template <typename S, int BC, bool OBS>
-__global__ void __launch_bounds__(kPairMaxThreads, OBS ? 4 : kPairMinBlocks) k_step_pair(
+template <typename S, int BC>
+__global__ void __launch_bounds__(kPairMaxThreads, kPairMinBlocks) k_step_pair(
     const S* __restrict__ src, S* __restrict__ dst, const float* __restrict__ phi_field,
     float* __restrict__ mac, const NodeParams<F2> P, const NodeParams<float> P1, const int nx,
     const int ny, const int64_t pitch, const int64_t plane, const float scale,
     const float inv_scale, const int write_macros, const uint32_t* __restrict__ tick_in,
-    uint32_t* __restrict__ tick_out, const float* __restrict__ um_in, float* __restrict__ um_out,
-    double* __restrict__ obs_part, const float* __restrict__ obs_prev) {
+    uint32_t* __restrict__ tick_out, const float* __restrict__ um_in, float* __restrict__ um_out) {
   grid_dep_wait();
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t tick = read_tick<S, float>(tick_in, tick_out);
-  if constexpr (OBS) {
-    FuseAcc<float> acc;
-    fuse_zero(acc);
-    const PairObs ob{&acc, obs_prev};
-    if (x0 < nx && y < ny) {
-      const bool full = x0 + 1 < nx;
-      const bool uniform = BC == BC_CAVITY ? (x0 > 0 && x0 + 2 < nx) : full;
-      if (uniform) {
-        step_pair<S, BC, true>(src, dst, phi_field, mac, P, x0, y, nx, ny, (uint32_t)pitch,
-                               (uint32_t)plane, scale, inv_scale, write_macros, tick, um_in,
-                               um_out, &ob);
-      } else if (BC == BC_CAVITY && full) {
-        step_pair_side<S, true>(src, dst, phi_field, mac, P, x0, y, nx, ny, (uint32_t)pitch,
-                                (uint32_t)plane, scale, inv_scale, write_macros, tick, um_in,
-                                um_out, &ob);
-      } else {
-        step_node<S, float, BC, true>(src, dst, phi_field, mac, P1, x0, y, nx, ny, pitch, plane,
-                                      scale, inv_scale, write_macros, tick, nullptr, um_in,
-                                      um_out, 0, &acc, obs_prev);
-        if (full)
-          step_node<S, float, BC, true>(src, dst, phi_field, mac, P1, x0 + 1, y, nx, ny, pitch,
-                                        plane, scale, inv_scale, write_macros, tick, nullptr,
-                                        um_in, um_out, 0, &acc, obs_prev);
-      }
-    }
-    fuse_block_store<float>(acc, obs_part);
-    return;
-  }
   if (x0 >= nx || y >= ny) return;
   const bool full = x0 + 1 < nx;
   const bool uniform = BC == BC_CAVITY ? (x0 > 0 && x0 + 2 < nx) : full;
@@ -482,17 +429,10 @@ cudaError_t launch_step_pair_t(const LatticeArgs& a, const NodeParams<double>& P
   const float* um_in = static_cast<const float*>(a.um_in);
   float* um_out = static_cast<float*>(a.um_out);
   cudaError_t e;
-  double* part = a.obs_part;
-  const float* prev = static_cast<const float*>(a.obs_prev);
 #define LTNE_PAIR_LAUNCH(bc)                                                                   \
-  e = part ? launch_kernel(a.chained != 0, k_step_pair<S, bc, true>, grid, block, 0, st, src,  \
-                           dst, phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale,          \
-                           inv_scale, a.write_macros, a.tick_in, a.tick_out, um_in, um_out,    \
-                           part, prev)                                                         \
-           : launch_kernel(a.chained != 0, k_step_pair<S, bc, false>, grid, block, 0, st, src, \
-                           dst, phi, mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale,          \
-                           inv_scale, a.write_macros, a.tick_in, a.tick_out, um_in, um_out,    \
-                           part, prev)
+  e = launch_kernel(a.chained != 0, k_step_pair<S, bc>, grid, block, 0, st, src, dst, phi,     \
+                    mac, P, P1, a.nx, a.ny, a.pitch, a.plane, scale, inv_scale,                \
+                    a.write_macros, a.tick_in, a.tick_out, um_in, um_out)
   switch (a.bc) {
     case BC_CAVITY: LTNE_PAIR_LAUNCH(BC_CAVITY); break;
     case BC_PERIODIC: LTNE_PAIR_LAUNCH(BC_PERIODIC); break;

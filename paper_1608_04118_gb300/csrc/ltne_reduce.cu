@@ -215,14 +215,6 @@ int reduce_blocks(int nx, int ny) {
   return ((nx + RB - 1) / RB) * ((ny + seg - 1) / seg);
 }
 
-cudaError_t launch_reduce_pass2(const ReduceArgs& a, cudaStream_t st) {
-  if (a.is_double)
-    k_reduce_pass2<double><<<NACC, RB, 0, st>>>(a);
-  else
-    k_reduce_pass2<float><<<NACC, RB, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
   const int seg = reduce_seg(a.nx, a.ny);
   dim3 grid((a.nx + RB - 1) / RB, (a.ny + seg - 1) / seg);

@@ -17,7 +17,7 @@
 // fields are written only on the last step of an ltne_step() call.
 #pragma once
 
-#include "ltne_fuse.cuh"
+#include "ltne_internal.h"
 
 namespace ltne {
 
@@ -128,9 +128,7 @@ __device__ __forceinline__ void store_macros(C* __restrict__ mac, int64_t plane,
 
 // One node (x, y) of one time step: pull, wall rebuild, macroscopic values,
 // collision, store.  Shared by the single-lattice and the batched kernels.
-// OBS: also add the node's observables terms to *oacc (obs_prev: the
-// residual reference's u_x plane, or null for none).
-template <typename S, typename C, int BC, bool OBS = false>
+template <typename S, typename C, int BC>
 __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restrict__ dst,
                                           const C* __restrict__ phi_field, C* __restrict__ mac,
                                           const NodeParams<C>& P, const int x, const int y,
@@ -140,9 +138,7 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
                                           C* __restrict__ pre_out = nullptr,
                                           const C* __restrict__ um_in = nullptr,
                                           C* __restrict__ um_out = nullptr,
-                                          const int slab_walls = 0,
-                                          FuseAcc<C>* oacc = nullptr,
-                                          const C* __restrict__ obs_prev = nullptr) {
+                                          const int slab_walls = 0) {
   // Wall classification and the node whose neighbourhood is pulled.
   int cx = x, cy = y;
   int kind = -1;  // -1 interior, 0 hot wall, 1 cold wall, 2 adiabatic / no-slip row
@@ -203,17 +199,6 @@ __device__ __forceinline__ void step_node(const S* __restrict__ src, S* __restri
   macros<C>(P, md, f, gf, gs, m);
   if (P.hv_local) um_out[off] = m.umag;  // u_m of Eq. 52 for the next state
   if (write_macros) store_macros<C>(mac, plane, off, m);
-  if constexpr (OBS) {
-    const uint32_t pl = (uint32_t)plane;
-    C pux = m.ux, puy = m.uy, pTf = m.dTf, pTs = m.dTs;
-    if (obs_prev) {
-      pux = obs_prev[off];
-      puy = obs_prev[pl + off];
-      pTf = obs_prev[2u * pl + off];
-      pTs = obs_prev[3u * pl + off];
-    }
-    fuse_node<C>(*oacc, m.drho, m.ux, m.uy, m.dTf, m.dTs, md.phi, P.sigma, pux, puy, pTf, pTs);
-  }
   collide<C>(P, m, f, gf, gs);
   Pops<S, C>::store(dst, plane, off, scale, f, gf, gs, (uint32_t)off, tick);
 }
@@ -233,9 +218,7 @@ __device__ __forceinline__ uint32_t read_tick(const uint32_t* __restrict__ tick_
   return tick;
 }
 
-// OBS: the last step of an ltne_step call, which also leaves the
-// observables' block partials (every thread of a block takes part).
-template <typename S, typename C, int BC, bool OBS>
+template <typename S, typename C, int BC>
 __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst,
                                               const C* __restrict__ phi_field,
                                               C* __restrict__ mac, const NodeParams<C> P,
@@ -245,23 +228,11 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
                                               const uint32_t* __restrict__ tick_in,
                                               uint32_t* __restrict__ tick_out,
                                               const C* __restrict__ um_in,
-                                              C* __restrict__ um_out, const int slab_walls,
-                                              double* __restrict__ obs_part,
-                                              const C* __restrict__ obs_prev) {
+                                              C* __restrict__ um_out, const int slab_walls) {
   grid_dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t tick = read_tick<S, C>(tick_in, tick_out);
-  if constexpr (OBS) {
-    FuseAcc<C> acc;
-    fuse_zero(acc);
-    if (x < nx && y < ny)
-      step_node<S, C, BC, true>(src, dst, phi_field, mac, P, x, y, nx, ny, pitch, plane, scale,
-                                inv_scale, write_macros, tick, nullptr, um_in, um_out,
-                                slab_walls, &acc, obs_prev);
-    fuse_block_store<C>(acc, obs_part);
-    return;
-  }
   if (x >= nx || y >= ny) return;
   if (BC == BC_SLAB && ((y == 0 && !(slab_walls & SLAB_LO_WALL)) ||
                         (y == ny - 1 && !(slab_walls & SLAB_HI_WALL))))
@@ -322,27 +293,16 @@ cudaError_t launch_step_t(const LatticeArgs& a, const NodeParams<double>& Pd, St
   C* um_out = static_cast<C*>(a.um_out);
   const bool ch = a.chained != 0;
   const dim3 g = grid, b = block;
-  double* part = a.obs_part;
-  const C* prev = static_cast<const C*>(a.obs_prev);
   cudaError_t e;
-#define LTNE_STEP_LAUNCH(bc, obs, walls)                                                       \
-  e = launch_kernel(ch, k_step<S, C, bc, obs>, g, b, 0, st, src, dst, phi, mac, P, a.nx, a.ny,  \
+#define LTNE_STEP_LAUNCH(bc, walls)                                                            \
+  e = launch_kernel(ch, k_step<S, C, bc>, g, b, 0, st, src, dst, phi, mac, P, a.nx, a.ny,       \
                     a.pitch, a.plane, scale, inv_scale, a.write_macros, a.tick_in, a.tick_out,  \
-                    um_in, um_out, walls, part, prev)
+                    um_in, um_out, walls)
   switch (a.bc) {
-    case BC_CAVITY:
-      if (part) LTNE_STEP_LAUNCH(BC_CAVITY, true, 0);
-      else LTNE_STEP_LAUNCH(BC_CAVITY, false, 0);
-      break;
-    case BC_PERIODIC:
-      if (part) LTNE_STEP_LAUNCH(BC_PERIODIC, true, 0);
-      else LTNE_STEP_LAUNCH(BC_PERIODIC, false, 0);
-      break;
-    case BC_CHANNEL:
-      if (part) LTNE_STEP_LAUNCH(BC_CHANNEL, true, 0);
-      else LTNE_STEP_LAUNCH(BC_CHANNEL, false, 0);
-      break;
-    case BC_SLAB: LTNE_STEP_LAUNCH(BC_SLAB, false, a.slab_walls); break;
+    case BC_CAVITY: LTNE_STEP_LAUNCH(BC_CAVITY, 0); break;
+    case BC_PERIODIC: LTNE_STEP_LAUNCH(BC_PERIODIC, 0); break;
+    case BC_CHANNEL: LTNE_STEP_LAUNCH(BC_CHANNEL, 0); break;
+    case BC_SLAB: LTNE_STEP_LAUNCH(BC_SLAB, a.slab_walls); break;
     default:
       return cudaErrorInvalidValue;
   }

@@ -50,8 +50,7 @@ def test_static_observables_match_workspace_observables():
     por = torch.from_numpy(phi.astype(np.float32)).to(dev)
     for call, steps in enumerate((400, 250)):
         cav.step(steps)
-        fused = cav.observables()  # the block partials the last step left
-        ref = cav.observables()    # no step since: the reduction pass over the fields
+        ref = cav.observables()
         f = cav.fields()
         # the caller's own copy of the fields: five planes of deviations
         # (rho - 1, ux, uy, T_f - T0, T_s - T0) with row pitch nx
@@ -66,9 +65,6 @@ def test_static_observables_match_workspace_observables():
         got = out.as_dict()
         for k in KEYS:
             assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-14), (call, k)
-            # the other summation order: FP32 sums of at most 32 nodes per
-            # partial in both, FP64 above (tests/test_gpu_observables.py)
-            assert got[k] == pytest.approx(fused[k], rel=1e-9, abs=1e-12), (call, k)
         assert got["step"] == ref["step"] and got["nonfinite"] == 0
         assert np.isnan(got["residual"])  # no snapshot is kept by this variant
 
