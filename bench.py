@@ -900,7 +900,7 @@ def main():
     from paper_1608_04118_gb300 import build as B
 
     B.build()
-    from paper_1608_04118_gb300.ltne import Cavity, LTNE_K_ERGUN
+    from paper_1608_04118_gb300.ltne import Cavity, FIELD_KEYS, LTNE_K_ERGUN
 
     c = W.C2_THROUGHPUT
     n = args.n
@@ -977,7 +977,11 @@ def main():
     e2e = None
     if not args.no_e2e:
         k = args.steps
-        host_out = {}
+        # the caller's host arrays for the fields, reused from run to run
+        # (allocated and first touched by one untimed run of the sequence)
+        host_out = {key: np.empty((n, n)) for key in FIELD_KEYS}
+        cav.set_fields(porosity=phi).step(1).fields(out=host_out)
+        cav.observables()
         barrier()
         t0 = time.perf_counter()
         cav.set_fields(porosity=phi)  # H2D of the porosity; the fields at rest, T = T_ref
@@ -986,7 +990,7 @@ def main():
         cav.step(k)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        host_out = cav.fields()       # D2H of the fields
+        cav.fields(out=host_out)      # D2H of the fields
         host_ob = cav.observables()   # D2H of the observables
         torch.cuda.synchronize()
         t3 = time.perf_counter()
@@ -999,7 +1003,8 @@ def main():
         e2e = {"value": whole_job_mlups(nodes, k, ws, tt), "unit": UNIT,
                "h2d_bytes_per_step": h2d / k, "d2h_bytes_per_step": d2h / k,
                "note": "whole run through the C ABI: set_fields from host arrays, %d steps, "
-                       "get_fields + observables to host" % k,
+                       "get_fields (into the caller's float64 arrays, reused) + observables "
+                       "to host" % k,
                "phases_s": {"set_fields": t1 - t0, "steps": t2 - t1,
                             "get_fields_and_observables": t3 - t2}}
         assert host_ob["nonfinite"] == 0 and np.isfinite(host_out["Tf"]).all()

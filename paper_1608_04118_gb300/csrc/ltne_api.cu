@@ -144,6 +144,20 @@ void host_chunks(int64_t n, F fn) {
   for (int c = 0; c < kHostChunks; ++c) chunk(c);
 }
 
+// The Ergun mean of a porosity field, mean(phi^3 / (1 - phi)^2) (Eq. 5 with
+// the Ergun permeability, solved for the diameter that gives mean K / L^2 =
+// Da): the terms summed in order within each of the kHostChunks chunks of
+// host_chunks, then the chunk sums in order.  Every path that forms it
+// (ltne_ergun_diameter, set_fields' staging pass) follows this order, so the
+// diameter is the same bits whichever computes it.
+inline double ergun_term(double ph) { return ph * ph * ph / ((1 - ph) * (1 - ph)); }
+inline int64_t ergun_chunk_len(int64_t n) { return (n + kHostChunks - 1) / kHostChunks; }
+inline double ergun_combine(const double* part, int64_t n) {
+  double acc = 0.0;
+  for (int c = 0; c < kHostChunks; ++c) acc += part[c];
+  return acc / (double)n;
+}
+
 // Pinned staging of whole fields between host arrays and the device planes:
 // rows go in blocks through two pinned buffers, so that converting one block
 // on the host overlaps the copy of the other.
@@ -241,19 +255,14 @@ double ergun_mean(const double* porosity, int64_t n) {
   double part[kHostChunks] = {0};
   host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
     double s = 0.0;
-    for (int64_t k = lo; k < hi; ++k) {
-      const double ph = porosity[k];
-      s += ph * ph * ph / ((1 - ph) * (1 - ph));
-    }
+    for (int64_t k = lo; k < hi; ++k) s += ergun_term(porosity[k]);
     part[c] = s;
   });
-  double acc = 0.0;
-  for (int c = 0; c < kHostChunks; ++c) acc += part[c];
-  return acc / (double)n;
+  return ergun_combine(part, n);
 }
 
 // Lattice constants from the problem statement.  Returns a status code.
-int derive_params(const ltne_params& p, const double* porosity, NodeParams<double>& P,
+int derive_params(const ltne_params& p, const double* erg_mean, NodeParams<double>& P,
                   DerivedInfo& info) {
   const double L = p.ny - 1.0;
   const double cs2 = 1.0 / 3.0;            // c_s^2 (below Eq. 23)
@@ -310,9 +319,8 @@ int derive_params(const ltne_params& p, const double* porosity, NodeParams<doubl
     if (d <= 0) {
       // mean over the nodes of phi^3 / (1-phi)^2, so that mean K/L^2 = Da
       double acc = 0.0;
-      const int64_t n = (int64_t)p.nx * p.ny;
-      if (porosity) {
-        acc = ergun_mean(porosity, n);
+      if (erg_mean) {
+        acc = *erg_mean;
       } else {
         const double ph = p.porosity;
         acc = ph * ph * ph / ((1 - ph) * (1 - ph));
@@ -429,11 +437,11 @@ int finish_observables(const ltne_params& p, const DerivedInfo& info, int64_t st
 
 namespace {
 
-int derive(ltne_handle* h, const double* porosity) {
+int derive(ltne_handle* h, const double* erg_mean) {
   DerivedInfo info;
   ltne_params pg = h->p;
   if (h->slab) pg.ny = h->gny;  // a slab takes the lattice constants of the whole cavity
-  const int rc = derive_params(pg, h->slab ? nullptr : porosity, h->P, info);
+  const int rc = derive_params(pg, h->slab ? nullptr : erg_mean, h->P, info);
   if (rc == LTNE_OK) {
     h->L = info.L;
     h->nu_f = info.nu_f;
@@ -562,27 +570,62 @@ cudaError_t build_graph(ltne_handle* h, int parity) {
 
 namespace ltne {
 
+// The porosity plane from the host array in one pass: every value checked
+// to lie in (0, 1), converted to the compute type and, when erg_part is
+// given, its Ergun term added to the running sum of its chunk -- the chunks
+// and order of ergun_mean, a chunk that spans two staged blocks continuing
+// its sum -- so that the diameter is the bits ltne_ergun_diameter gives.
+// INVALID_ARG on a value out of range.
+static int stage_porosity(ltne_handle* h, const double* phi, double* erg_part) {
+  const int nx = h->p.nx;
+  const int64_t len = ergun_chunk_len((int64_t)nx * h->p.ny);
+  const bool dbl = h->ec == 8;
+  return upload_field(h, h->ws + h->off_phi, [&](char* buf, int y0, int y1) {
+    const int64_t base = (int64_t)y0 * nx, end = (int64_t)y1 * nx;
+    const int c0 = (int)(base / len), c1 = (int)((end - 1) / len);
+    bool bad[kHostChunks] = {false};
+    // job j: the part of chunk c0 + j inside [base, end)
+    const std::function<void(int)> job = [&](int j) {
+      const int c = c0 + j;
+      const int64_t lo = std::max(base, (int64_t)c * len), hi = std::min(end, (int64_t)(c + 1) * len);
+      double s = erg_part ? erg_part[c] : 0.0;
+      for (int64_t k = lo; k < hi; ++k) {
+        const double v = phi[k];
+        if (!in_open(v, 0.0, 1.0)) {
+          bad[c] = true;
+          return;
+        }
+        if (dbl) reinterpret_cast<double*>(buf)[k - base] = v;
+        else reinterpret_cast<float*>(buf)[k - base] = (float)v;
+        if (erg_part) s += ergun_term(v);
+      }
+      if (erg_part) erg_part[c] = s;
+    };
+    const int jobs = c1 - c0 + 1;
+    if (end - base < ((int64_t)1 << 18) || !HostPool::get().run(jobs, job))
+      for (int j = 0; j < jobs; ++j) job(j);
+    for (int c = c0; c <= c1; ++c)
+      if (bad[c]) return false;
+    return true;
+  });
+}
+
 int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, const double* ux,
                     const double* uy, const double* T_f, const double* T_s, void* pre_out) {
   if (!h) return LTNE_ERR_INVALID_ARG;
   if (!h->ws) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;
   if ((porosity != nullptr) != (p.porosity_field != 0)) return LTNE_ERR_INVALID_ARG;
-  const int64_t n = (int64_t)p.nx * p.ny;
-  if (porosity) {
-    bool bad[kHostChunks] = {false};
-    host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
-      for (int64_t k = lo; k < hi; ++k)
-        if (!in_open(porosity[k], 0.0, 1.0)) {
-          bad[c] = true;
-          return;
-        }
-    });
-    for (int c = 0; c < kHostChunks; ++c)
-      if (bad[c]) return LTNE_ERR_INVALID_ARG;
-  }
-  int rc = derive(h, porosity);
+  // The constants are checked before any device work; with a porosity field
+  // the Ergun diameter waits for the staging pass below, which checks and
+  // converts the field and forms the Ergun mean in one read of it (any
+  // positive mean derives the same constants but the diameter).
+  const double any_mean = 1.0;
+  int rc = derive(h, porosity ? &any_mean : nullptr);
   if (rc != LTNE_OK) return rc;
+  // From here the device state is being replaced: a failure below leaves
+  // the handle without fields until a set_fields call succeeds.
+  h->fields_set = false;
   drop_graphs(h);  // kernel arguments captured in graphs depend on the parameters
 
   // Zero the whole workspace first -- population buffers, porosity, both
@@ -639,8 +682,15 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
     if (rc != LTNE_OK) return rc;
   }
   if (porosity) {
-    rc = stage(porosity, 0.0, 0.0, h->ws + h->off_phi);
+    const bool erg = p.permeability == LTNE_K_ERGUN && !(p.d_p > 0) && !h->slab;
+    double part[kHostChunks] = {0};
+    rc = stage_porosity(h, porosity, erg ? part : nullptr);
     if (rc != LTNE_OK) return rc;
+    if (erg) {
+      const double mean = ergun_combine(part, (int64_t)p.nx * p.ny);
+      rc = derive(h, &mean);
+      if (rc != LTNE_OK) return rc;
+    }
   }
   // the step counters and the device error word start cleared
   cudaError_t e = cudaMemsetAsync(h->ws + h->off_tick, 0, 3 * sizeof(uint32_t), h->stream);

@@ -146,7 +146,10 @@ struct DerivedInfo {
   double d_ergun = 0;  // Ergun particle diameter in use (0: Darcy permeability)
 };
 int validate_params(const ltne_params& p);
-int derive_params(const ltne_params& p, const double* porosity, NodeParams<double>& P,
+// erg_mean: the mean of phi^3 / (1 - phi)^2 over a per-node porosity field
+// (nullptr: the uniform porosity's value); it fixes the Ergun diameter when
+// none is given
+int derive_params(const ltne_params& p, const double* erg_mean, NodeParams<double>& P,
                   DerivedInfo& info);
 int finish_observables(const ltne_params& p, const DerivedInfo& info, int64_t step,
                        bool have_prev, const double* acc, ltne_obs* out);

@@ -220,11 +220,23 @@ def ltne_observables(h, allow_nonfinite=False) -> dict:
     return o.as_dict()
 
 
-def ltne_get_fields(h, nx, ny) -> dict:
-    out = {k: np.empty(nx * ny) for k in ("rho", "ux", "uy", "Tf", "Ts")}
-    _check(_lib().ltne_get_fields(h, *[_ptr(out[k]) for k in ("rho", "ux", "uy", "Tf", "Ts")]),
-           "ltne_get_fields")
-    return {k: v.reshape(ny, nx) for k, v in out.items()}
+FIELD_KEYS = ("rho", "ux", "uy", "Tf", "Ts")
+
+
+def ltne_get_fields(h, nx, ny, out=None) -> dict:
+    """The five fields as (ny, nx) float64 arrays; ``out`` may hold arrays of
+    that shape and type (C-contiguous) to be filled instead of new ones."""
+    if out is None:
+        out = {k: np.empty((ny, nx)) for k in FIELD_KEYS}
+    else:
+        for k in FIELD_KEYS:
+            a = out[k]
+            if (not isinstance(a, np.ndarray) or a.dtype != np.float64 or a.shape != (ny, nx)
+                    or not a.flags.c_contiguous or not a.flags.writeable):
+                raise ValueError("out[%r] must be a writeable C-contiguous float64 array of "
+                                 "shape (%d, %d)" % (k, ny, nx))
+    _check(_lib().ltne_get_fields(h, *[_ptr(out[k]) for k in FIELD_KEYS]), "ltne_get_fields")
+    return {k: out[k] for k in FIELD_KEYS}
 
 
 def ltne_state_bytes(h) -> int:
@@ -439,8 +451,9 @@ class Cavity:
     def observables(self, allow_nonfinite=False):
         return ltne_observables(self.h, allow_nonfinite)
 
-    def fields(self):
-        return ltne_get_fields(self.h, self.nx, self.ny)
+    def fields(self, out=None):
+        """The fields as (ny, nx) float64 arrays (into ``out`` if given)."""
+        return ltne_get_fields(self.h, self.nx, self.ny, out)
 
     def get_state(self):
         return ltne_get_state(self.h)
