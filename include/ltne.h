@@ -190,6 +190,29 @@ int ltne_observables(ltne_handle* h, ltne_obs* out);
 int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double* T_f,
                     double* T_s);
 
+/* How ltne_set_fields and ltne_get_fields move whole fields between the
+   caller's host arrays and the device (no counterpart in the paper).
+   LTNE_HOST_IO_STAGED: host threads convert the values (absolute FP64 <->
+   deviations in the compute type) through two pinned buffers that are
+   copied while the other is converted; any GPU.  LTNE_HOST_IO_DIRECT:
+   kernels read and write the caller's arrays themselves and convert on the
+   device, for GPUs that reach pageable host memory through the host's page
+   tables (GB300 with Grace memory over NVLink-C2C); ltne_set_fields then
+   returns only after the arrays were read (the Ergun mean is formed on the
+   host meanwhile), and ltne_get_fields writes directly only into
+   page-locked arrays (pinned or registered; pageable ones are staged: a
+   device write to a page the host never touched costs a host-serviced
+   fault per page).  LTNE_HOST_IO_AUTO (the default): DIRECT where the
+   device supports it, else STAGED.  Both forms give the same bits and the
+   same errors.  ltne_set_host_io: INVALID_ARG for an unknown mode or for
+   DIRECT on a device without that access.  ltne_get_host_io: the form in
+   use (STAGED or DIRECT). */
+#define LTNE_HOST_IO_AUTO 0
+#define LTNE_HOST_IO_STAGED 1
+#define LTNE_HOST_IO_DIRECT 2
+int ltne_set_host_io(ltne_handle* h, int32_t mode);
+int ltne_get_host_io(ltne_handle* h, int32_t* mode);
+
 /* Checkpoint: size of the state blob, and copies of it to / from host
    memory.  The blob holds the populations, the macroscopic fields, the
    per-node porosity (if any), the previous |u| of the local h_v model (if

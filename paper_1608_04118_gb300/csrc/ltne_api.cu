@@ -474,8 +474,10 @@ void layout(ltne_handle* h) {
   off = align_up(off + (size_t)h->red_blocks * NACC * sizeof(double), A);
   h->off_out = off;
   off = align_up(off + NACC * sizeof(double), A);
-  h->off_tick = off;  // two uint32 step counters for the stochastic rounding, then
-  off = align_up(off + 3 * sizeof(uint32_t), A);  // the device error word
+  // two uint32 step counters for the stochastic rounding, the device error
+  // word, and the flag set_fields' host-reading kernels raise on a bad value
+  h->off_tick = off;
+  off = align_up(off + 4 * sizeof(uint32_t), A);
   for (int b = 0; b < 2; ++b) {  // |u| of the previous state per buffer (Eq. 52)
     h->off_um[b] = off;
     if (p.hv_local) off = align_up(off + (size_t)h->plane * h->ec, A);
@@ -569,6 +571,58 @@ cudaError_t build_graph(ltne_handle* h, int parity) {
 }  // namespace
 
 namespace ltne {
+
+// Whether kernels may read and write the caller's host arrays directly: the
+// current device reaches pageable host memory through the host's page
+// tables (asked once per handle).
+static bool device_reads_host_pages(ltne_handle* h) {
+  if (h->direct_io < 0) {
+    int dev = 0, a = 0, b = 0;
+    h->direct_io = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) ==
+            cudaSuccess)
+      h->direct_io = (a && b) ? 1 : 0;
+    cudaGetLastError();
+  }
+  return h->direct_io == 1;
+}
+
+static bool direct_host_io(ltne_handle* h) {
+  return h->host_io != LTNE_HOST_IO_STAGED && device_reads_host_pages(h);
+}
+
+// Whether every non-null pointer is memory a kernel reaches without a
+// page fault (page-locked host memory, or device or managed memory).  A
+// kernel's write to a pageable page the host never touched costs a fault
+// serviced by the host per page: 175 ms for the five fields of a 4096^2
+// lattice into fresh arrays against 11 ms staged, so writes into pageable
+// arrays are staged.
+static bool all_page_locked(double* const* p, int n) {
+  for (int k = 0; k < n; ++k) {
+    if (!p[k]) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p[k]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost && a.type != cudaMemoryTypeDevice &&
+        a.type != cudaMemoryTypeManaged)
+      return false;
+  }
+  return true;
+}
+
+// The pinned landing place of the observables' accumulators and of one
+// device word (allocated at first use, freed by ltne_destroy).
+static cudaError_t ensure_pin_obs(ltne_handle* h) {
+  if (h->pin_obs) return cudaSuccess;
+  const cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&h->pin_obs),
+                                      (NACC + 1) * sizeof(double), cudaHostAllocDefault);
+  if (e != cudaSuccess) h->pin_obs = nullptr;
+  return e;
+}
 
 // The porosity plane from the host array in one pass: every value checked
 // to lie in (0, 1), converted to the compute type and, when erg_part is
@@ -676,21 +730,55 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   };
   h->mcur = 0;  // the fields go to macro set 0; no residual snapshot yet
   h->msnap = -1;
-  for (int k = 0; k < 5; ++k) {
-    if (!src[k]) continue;
-    rc = stage(src[k], defaults[k], refs[k], mac_cur(h) + (size_t)k * h->plane * h->ec);
-    if (rc != LTNE_OK) return rc;
-  }
-  if (porosity) {
-    const bool erg = p.permeability == LTNE_K_ERGUN && !(p.d_p > 0) && !h->slab;
-    double part[kHostChunks] = {0};
-    rc = stage_porosity(h, porosity, erg ? part : nullptr);
-    if (rc != LTNE_OK) return rc;
-    if (erg) {
-      const double mean = ergun_combine(part, (int64_t)p.nx * p.ny);
-      rc = derive(h, &mean);
+  const bool erg = porosity && p.permeability == LTNE_K_ERGUN && !(p.d_p > 0) && !h->slab;
+  double erg_mean = 0.0;
+  if (direct_host_io(h)) {
+    // kernels read the host arrays, convert and check them; meanwhile the
+    // host forms the Ergun mean (ergun_mean, the order every path uses)
+    HostPlanes hp;
+    bool any = false;
+    for (int k = 0; k < 5; ++k)
+      if (src[k]) {
+        hp.src[k] = src[k];
+        hp.ref[k] = refs[k];
+        any = true;
+      }
+    uint32_t* bad = reinterpret_cast<uint32_t*>(h->ws + h->off_tick) + 3;
+    cudaError_t e = ensure_pin_obs(h);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess && any)
+      e = launch_fields_from_host(mac_cur(h), dbl, h->plane, h->pitch, nx, p.ny, hp, bad,
+                                  h->stream);
+    if (e == cudaSuccess && porosity)
+      e = launch_porosity_from_host(porosity, h->ws + h->off_phi, dbl, h->pitch, nx, p.ny, bad,
+                                    h->stream);
+    uint32_t* flag = reinterpret_cast<uint32_t*>(h->pin_obs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(flag, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(h->stream);  // no kernel may still read the caller's arrays
+      return fail_cuda(e);
+    }
+    if (erg) erg_mean = ergun_mean(porosity, (int64_t)p.nx * p.ny);
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (*flag) return LTNE_ERR_INVALID_ARG;
+  } else {
+    for (int k = 0; k < 5; ++k) {
+      if (!src[k]) continue;
+      rc = stage(src[k], defaults[k], refs[k], mac_cur(h) + (size_t)k * h->plane * h->ec);
       if (rc != LTNE_OK) return rc;
     }
+    if (porosity) {
+      double part[kHostChunks] = {0};
+      rc = stage_porosity(h, porosity, erg ? part : nullptr);
+      if (rc != LTNE_OK) return rc;
+      if (erg) erg_mean = ergun_combine(part, (int64_t)p.nx * p.ny);
+    }
+  }
+  if (erg) {
+    rc = derive(h, &erg_mean);
+    if (rc != LTNE_OK) return rc;
   }
   // the step counters and the device error word start cleared
   cudaError_t e = cudaMemsetAsync(h->ws + h->off_tick, 0, 3 * sizeof(uint32_t), h->stream);
@@ -952,14 +1040,8 @@ int ltne_observables(ltne_handle* h, ltne_obs* out) {
   if (!h->ws || !h->fields_set) return LTNE_ERR_STATE;
   const ltne_params& p = h->p;
   cudaError_t e = cudaSuccess;
-  if (!h->pin_obs) {
-    e = cudaHostAlloc(reinterpret_cast<void**>(&h->pin_obs), (NACC + 1) * sizeof(double),
-                      cudaHostAllocDefault);
-    if (e != cudaSuccess) {
-      h->pin_obs = nullptr;
-      return fail_cuda(e);
-    }
-  }
+  e = ensure_pin_obs(h);
+  if (e != cudaSuccess) return fail_cuda(e);
   const int rr = reduce_launch(h);
   if (rr != LTNE_OK) return rr;
   // the accumulators and the device error word in one read-back: a staged
@@ -996,6 +1078,17 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
   const ltne_params& p = h->p;
   double* dst[5] = {rho, ux, uy, T_f, T_s};
   const int nx = p.nx;
+  if (direct_host_io(h) && all_page_locked(dst, 5)) {  // one kernel writes the caller's arrays
+    HostPlanes hp;
+    for (int k = 0; k < 5; ++k) {
+      hp.dst[k] = dst[k];
+      hp.ref[k] = (k == 0) ? 1.0 : (k >= 3 ? p.T_ref : 0.0);  // planes hold deviations
+    }
+    cudaError_t e = launch_fields_to_host(mac_cur(h), h->ec == 8, h->plane, h->pitch, nx, p.ny,
+                                          hp, h->stream);
+    const cudaError_t es = cudaStreamSynchronize(h->stream);
+    return fail_cuda(e != cudaSuccess ? e : es);
+  }
   for (int k = 0; k < 5; ++k) {
     if (!dst[k]) continue;
     const double ref = (k == 0) ? 1.0 : (k >= 3 ? p.T_ref : 0.0);  // planes hold deviations
@@ -1331,6 +1424,19 @@ int ltne_ergun_diameter(const double* porosity, int64_t n, double L, double Da, 
   for (int64_t k = 0; k < n; ++k)
     if (!in_open(porosity[k], 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
   *d = L * sqrt(150.0 * Da / ergun_mean(porosity, n));
+  return LTNE_OK;
+}
+
+int ltne_set_host_io(ltne_handle* h, int32_t mode) {
+  if (!h || mode < LTNE_HOST_IO_AUTO || mode > LTNE_HOST_IO_DIRECT) return LTNE_ERR_INVALID_ARG;
+  if (mode == LTNE_HOST_IO_DIRECT && !device_reads_host_pages(h)) return LTNE_ERR_INVALID_ARG;
+  h->host_io = mode;
+  return LTNE_OK;
+}
+
+int ltne_get_host_io(ltne_handle* h, int32_t* mode) {
+  if (!h || !mode) return LTNE_ERR_INVALID_ARG;
+  *mode = direct_host_io(h) ? LTNE_HOST_IO_DIRECT : LTNE_HOST_IO_STAGED;
   return LTNE_OK;
 }
 

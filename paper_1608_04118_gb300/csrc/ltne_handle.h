@@ -39,8 +39,15 @@ struct ltne_handle {
   int64_t launches = 0;
   int32_t adj_sched = 0;  // LTNE_ADJ_*
   // two pinned host buffers that stage whole fields in and out (allocated
-  // at the first set_fields / get_fields, freed by ltne_destroy)
+  // at the first set_fields / get_fields, freed by ltne_destroy), with an
+  // event per buffer marking its last copy
   char* pin[2] = {nullptr, nullptr};
+  cudaEvent_t pin_ev[2] = {nullptr, nullptr};
+  size_t pin_bytes = 0;
+  // host I/O form (LTNE_HOST_IO_*) and whether the device reaches pageable
+  // host memory through the host's page tables (-1: not asked yet)
+  int32_t host_io = LTNE_HOST_IO_AUTO;
+  int direct_io = -1;
   // Row slab of a cavity advanced by one process (ltne_create_slab): the
   // local lattice is the slab's computed rows with a halo row towards each
   // neighbouring slab; p.ny counts the local rows, gny the cavity's.
@@ -53,8 +60,6 @@ struct ltne_handle {
   // pinned landing place of the observables' accumulators and the device
   // error word (one asynchronous read-back per ltne_observables call)
   double* pin_obs = nullptr;
-  cudaEvent_t pin_ev[2] = {nullptr, nullptr};
-  size_t pin_bytes = 0;
 };
 
 namespace ltne {

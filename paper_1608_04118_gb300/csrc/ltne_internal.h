@@ -135,6 +135,22 @@ cudaError_t launch_halo_pack(const void* pops, int64_t pitch, int64_t plane, int
 cudaError_t launch_halo_unpack(void* pops, int64_t pitch, int64_t plane, int nx, int halo_lo,
                                int halo_hi, size_t es, const void* recv_lo, const void* recv_hi,
                                cudaStream_t st);
+// Whole fields between the caller's host arrays (row-major nx x ny, FP64,
+// absolute values) and the device planes (deviations ref subtracted, compute
+// type), moved by kernels that access the host arrays themselves
+// (ltne_hostio.cu); for GPUs that reach pageable host memory through the
+// host's page tables.  A null src / dst skips that plane.
+struct HostPlanes {
+  const double* src[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* dst[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double ref[5] = {0, 0, 0, 0, 0};
+};
+cudaError_t launch_fields_to_host(const void* mac, bool dbl, int64_t plane, int64_t pitch, int nx,
+                                  int ny, const HostPlanes& hp, cudaStream_t s);
+cudaError_t launch_fields_from_host(void* mac, bool dbl, int64_t plane, int64_t pitch, int nx,
+                                    int ny, const HostPlanes& hp, uint32_t* bad, cudaStream_t s);
+cudaError_t launch_porosity_from_host(const double* phi, void* dst, bool dbl, int64_t pitch, int nx,
+                                      int ny, uint32_t* bad, cudaStream_t s);
 // Mean of phi^3 / (1 - phi)^2 over n porosities, summed in a fixed order
 // (the Ergun particle diameter follows from it).
 double ergun_mean(const double* porosity, int64_t n);

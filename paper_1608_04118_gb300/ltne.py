@@ -28,6 +28,7 @@ LTNE_ERR_WORKSPACE = 7
 LTNE_F64, LTNE_F32, LTNE_F16DEV, LTNE_BF16DEV = 0, 1, 2, 3
 LTNE_BC_CAVITY, LTNE_BC_PERIODIC, LTNE_BC_CHANNEL = 0, 1, 2
 LTNE_ADJ_AUTO, LTNE_ADJ_ONE_WAVE, LTNE_ADJ_CAPPED = 0, 1, 2
+LTNE_HOST_IO_AUTO, LTNE_HOST_IO_STAGED, LTNE_HOST_IO_DIRECT = 0, 1, 2
 LTNE_K_DARCY, LTNE_K_ERGUN = 0, 1
 
 STORAGE = {"f64": LTNE_F64, "f32": LTNE_F32, "f16": LTNE_F16DEV, "bf16": LTNE_BF16DEV}
@@ -97,6 +98,8 @@ SIGNATURES = {
     "ltne_step_slabs": (C.c_int, [_vp, C.c_int32, C.c_int64, _vp, C.c_size_t]),
     "ltne_check_bounded_wait": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32)]),
     "ltne_get_staging": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
+    "ltne_set_host_io": (C.c_int, [_vp, C.c_int32]),
+    "ltne_get_host_io": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "ltne_observables_static": (C.c_int, [C.POINTER(ltne_params), _vp, C.c_int64, _vp, C.c_int64,
                                           _vp, C.POINTER(ltne_obs)]),
     "ltne_set_adjoint_schedule": (C.c_int, [_vp, C.c_int32]),
@@ -300,6 +303,16 @@ def ltne_get_staging(h) -> int:
     return v.value
 
 
+def ltne_set_host_io(h, mode):
+    _check(_lib().ltne_set_host_io(h, int(mode)), "ltne_set_host_io")
+
+
+def ltne_get_host_io(h) -> int:
+    v = C.c_int32()
+    _check(_lib().ltne_get_host_io(h, C.byref(v)), "ltne_get_host_io")
+    return v.value
+
+
 def ltne_get_schedule(h):
     bx, by, npt = C.c_int32(), C.c_int32(), C.c_int32()
     _check(_lib().ltne_get_schedule(h, C.byref(bx), C.byref(by), C.byref(npt)),
@@ -498,6 +511,18 @@ class Cavity:
     @property
     def staging(self):
         return ltne_get_staging(self.h)
+
+    def set_host_io(self, mode):
+        """How set_fields / fields move host arrays: LTNE_HOST_IO_AUTO,
+        _STAGED (pinned buffers, host conversion) or _DIRECT (kernels read
+        and write the host arrays)."""
+        ltne_set_host_io(self.h, mode)
+        return self
+
+    @property
+    def host_io(self):
+        """The host I/O form in use (LTNE_HOST_IO_STAGED or _DIRECT)."""
+        return ltne_get_host_io(self.h)
 
     def set_adjoint_schedule(self, mode):
         """Register budget of the adjoint's transposed collision: 0 by lattice
