@@ -198,8 +198,9 @@ int ltne_get_fields(ltne_handle* h, double* rho, double* ux, double* uy, double*
    kernels read and write the caller's arrays themselves and convert on the
    device, for GPUs that reach pageable host memory through the host's page
    tables (GB300 with Grace memory over NVLink-C2C); ltne_set_fields then
-   returns only after the arrays were read (the Ergun mean is formed on the
-   host meanwhile), and ltne_get_fields writes directly only into
+   returns only after the arrays were read (the porosity kernel also forms
+   the Ergun mean, in the summation order ltne_ergun_diameter takes), and
+   ltne_get_fields writes directly only into
    page-locked arrays (pinned or registered; pageable ones are staged: a
    device write to a page the host never touched costs a host-serviced
    fault per page).  LTNE_HOST_IO_AUTO (the default): DIRECT where the

@@ -15,6 +15,7 @@
 #include <mutex>
 #include <thread>
 #include <vector>
+#include <vector>
 
 #include "ltne.h"
 #include "ltne_internal.h"
@@ -133,29 +134,16 @@ class HostPool {
   bool stop_ = false;
 };
 
+// (min_pool: the smallest n worth waking the pool for)
 template <typename F>
-void host_chunks(int64_t n, F fn) {
+void host_chunks(int64_t n, F fn, int64_t min_pool = (int64_t)1 << 18) {
   const int64_t len = (n + kHostChunks - 1) / kHostChunks;
   auto chunk = [&](int c) {
     const int64_t lo = (int64_t)c * len, hi = std::min(n, lo + len);
     if (lo < hi) fn(c, lo, hi);
   };
-  if (n >= ((int64_t)1 << 18) && HostPool::get().run(kHostChunks, chunk)) return;
+  if (n >= min_pool && HostPool::get().run(kHostChunks, chunk)) return;
   for (int c = 0; c < kHostChunks; ++c) chunk(c);
-}
-
-// The Ergun mean of a porosity field, mean(phi^3 / (1 - phi)^2) (Eq. 5 with
-// the Ergun permeability, solved for the diameter that gives mean K / L^2 =
-// Da): the terms summed in order within each of the kHostChunks chunks of
-// host_chunks, then the chunk sums in order.  Every path that forms it
-// (ltne_ergun_diameter, set_fields' staging pass) follows this order, so the
-// diameter is the same bits whichever computes it.
-inline double ergun_term(double ph) { return ph * ph * ph / ((1 - ph) * (1 - ph)); }
-inline int64_t ergun_chunk_len(int64_t n) { return (n + kHostChunks - 1) / kHostChunks; }
-inline double ergun_combine(const double* part, int64_t n) {
-  double acc = 0.0;
-  for (int c = 0; c < kHostChunks; ++c) acc += part[c];
-  return acc / (double)n;
 }
 
 // Pinned staging of whole fields between host arrays and the device planes:
@@ -251,14 +239,34 @@ int download_field(ltne_handle* h, const char* dev, Drain drain) {
 
 namespace ltne {
 
+double ergun_mean_of_chunks(const double* part, int64_t n) {
+  double acc = 0.0;
+  for (int64_t c = 0, m = ergun_chunks(n); c < m; ++c) acc += part[c];
+  return acc / (double)n;
+}
+
 double ergun_mean(const double* porosity, int64_t n) {
-  double part[kHostChunks] = {0};
-  host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
-    double s = 0.0;
-    for (int64_t k = lo; k < hi; ++k) s += ergun_term(porosity[k]);
-    part[c] = s;
-  });
-  return ergun_combine(part, n);
+  std::vector<double> part((size_t)ergun_chunks(n));
+  host_chunks(
+      (int64_t)part.size(),
+      [&](int, int64_t lo, int64_t hi) {
+        for (int64_t c = lo; c < hi; ++c) {
+          double v[kErgunLanes];
+          for (int l = 0; l < kErgunLanes; ++l) {
+            double s = 0.0;
+            for (int j = 0; j < kErgunPerLane; ++j) {
+              const int64_t i = c * kErgunChunk + (int64_t)j * kErgunLanes + l;
+              if (i < n) s += ergun_term(porosity[i]);
+            }
+            v[l] = s;
+          }
+          for (int st = kErgunLanes / 2; st >= 1; st >>= 1)
+            for (int l = 0; l < st; ++l) v[l] += v[l + st];
+          part[(size_t)c] = v[0];
+        }
+      },
+      64);
+  return ergun_mean_of_chunks(part.data(), n);
 }
 
 // Lattice constants from the problem statement.  Returns a status code.
@@ -624,41 +632,27 @@ static cudaError_t ensure_pin_obs(ltne_handle* h) {
   return e;
 }
 
-// The porosity plane from the host array in one pass: every value checked
-// to lie in (0, 1), converted to the compute type and, when erg_part is
-// given, its Ergun term added to the running sum of its chunk -- the chunks
-// and order of ergun_mean, a chunk that spans two staged blocks continuing
-// its sum -- so that the diameter is the bits ltne_ergun_diameter gives.
+// The porosity plane from the host array through the pinned buffers: every
+// value checked to lie in (0, 1) and converted to the compute type.
 // INVALID_ARG on a value out of range.
-static int stage_porosity(ltne_handle* h, const double* phi, double* erg_part) {
+static int stage_porosity(ltne_handle* h, const double* phi) {
   const int nx = h->p.nx;
-  const int64_t len = ergun_chunk_len((int64_t)nx * h->p.ny);
   const bool dbl = h->ec == 8;
   return upload_field(h, h->ws + h->off_phi, [&](char* buf, int y0, int y1) {
-    const int64_t base = (int64_t)y0 * nx, end = (int64_t)y1 * nx;
-    const int c0 = (int)(base / len), c1 = (int)((end - 1) / len);
+    const int64_t base = (int64_t)y0 * nx, cnt = (int64_t)(y1 - y0) * nx;
     bool bad[kHostChunks] = {false};
-    // job j: the part of chunk c0 + j inside [base, end)
-    const std::function<void(int)> job = [&](int j) {
-      const int c = c0 + j;
-      const int64_t lo = std::max(base, (int64_t)c * len), hi = std::min(end, (int64_t)(c + 1) * len);
-      double s = erg_part ? erg_part[c] : 0.0;
+    host_chunks(cnt, [&](int c, int64_t lo, int64_t hi) {
       for (int64_t k = lo; k < hi; ++k) {
-        const double v = phi[k];
+        const double v = phi[base + k];
         if (!in_open(v, 0.0, 1.0)) {
           bad[c] = true;
           return;
         }
-        if (dbl) reinterpret_cast<double*>(buf)[k - base] = v;
-        else reinterpret_cast<float*>(buf)[k - base] = (float)v;
-        if (erg_part) s += ergun_term(v);
+        if (dbl) reinterpret_cast<double*>(buf)[k] = v;
+        else reinterpret_cast<float*>(buf)[k] = (float)v;
       }
-      if (erg_part) erg_part[c] = s;
-    };
-    const int jobs = c1 - c0 + 1;
-    if (end - base < ((int64_t)1 << 18) || !HostPool::get().run(jobs, job))
-      for (int j = 0; j < jobs; ++j) job(j);
-    for (int c = c0; c <= c1; ++c)
+    });
+    for (int c = 0; c < kHostChunks; ++c)
       if (bad[c]) return false;
     return true;
   });
@@ -733,8 +727,8 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   const bool erg = porosity && p.permeability == LTNE_K_ERGUN && !(p.d_p > 0) && !h->slab;
   double erg_mean = 0.0;
   if (direct_host_io(h)) {
-    // kernels read the host arrays, convert and check them; meanwhile the
-    // host forms the Ergun mean (ergun_mean, the order every path uses)
+    // kernels read the host arrays, convert and check them; the porosity
+    // kernel also forms the Ergun chunk sums (the order of ergun_mean)
     HostPlanes hp;
     bool any = false;
     for (int k = 0; k < 5; ++k)
@@ -749,20 +743,30 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
     if (e == cudaSuccess && any)
       e = launch_fields_from_host(mac_cur(h), dbl, h->plane, h->pitch, nx, p.ny, hp, bad,
                                   h->stream);
+    // the chunk sums go to the reduction partials (room checked), then to
+    // the first pinned staging buffer
+    const int64_t n = (int64_t)p.nx * p.ny, chunks = ergun_chunks(n);
+    const bool erg_dev = erg && (size_t)chunks <= (size_t)h->red_blocks * NACC;
+    double* part = reinterpret_cast<double*>(h->ws + h->off_part);
+    if (e == cudaSuccess && erg_dev) e = ensure_pinned(h, (size_t)chunks * sizeof(double));
     if (e == cudaSuccess && porosity)
-      e = launch_porosity_from_host(porosity, h->ws + h->off_phi, dbl, h->pitch, nx, p.ny, bad,
-                                    h->stream);
+      e = launch_porosity_from_host(porosity, h->ws + h->off_phi, dbl, h->pitch, nx, p.ny,
+                                    erg_dev ? part : nullptr, bad, h->stream);
     uint32_t* flag = reinterpret_cast<uint32_t*>(h->pin_obs);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(flag, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && erg_dev)
+      e = cudaMemcpyAsync(h->pin[0], part, (size_t)chunks * sizeof(double),
+                          cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) {
       cudaStreamSynchronize(h->stream);  // no kernel may still read the caller's arrays
       return fail_cuda(e);
     }
-    if (erg) erg_mean = ergun_mean(porosity, (int64_t)p.nx * p.ny);
+    if (erg && !erg_dev) erg_mean = ergun_mean(porosity, n);
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail_cuda(e);
     if (*flag) return LTNE_ERR_INVALID_ARG;
+    if (erg_dev) erg_mean = ergun_mean_of_chunks(reinterpret_cast<const double*>(h->pin[0]), n);
   } else {
     for (int k = 0; k < 5; ++k) {
       if (!src[k]) continue;
@@ -770,10 +774,9 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
       if (rc != LTNE_OK) return rc;
     }
     if (porosity) {
-      double part[kHostChunks] = {0};
-      rc = stage_porosity(h, porosity, erg ? part : nullptr);
+      rc = stage_porosity(h, porosity);
       if (rc != LTNE_OK) return rc;
-      if (erg) erg_mean = ergun_combine(part, (int64_t)p.nx * p.ny);
+      if (erg) erg_mean = ergun_mean(porosity, (int64_t)p.nx * p.ny);
     }
   }
   if (erg) {
@@ -1421,8 +1424,12 @@ int ltne_observables_from_accumulators(const ltne_params* p, int64_t step, int32
 
 int ltne_ergun_diameter(const double* porosity, int64_t n, double L, double Da, double* d) {
   if (!porosity || n < 1 || !d || !(L > 0) || !(Da > 0)) return LTNE_ERR_INVALID_ARG;
-  for (int64_t k = 0; k < n; ++k)
-    if (!in_open(porosity[k], 0.0, 1.0)) return LTNE_ERR_INVALID_ARG;
+  bool bad[kHostChunks] = {false};
+  host_chunks(n, [&](int c, int64_t lo, int64_t hi) {
+    for (int64_t k = lo; k < hi && !bad[c]; ++k) bad[c] = !in_open(porosity[k], 0.0, 1.0);
+  });
+  for (int c = 0; c < kHostChunks; ++c)
+    if (bad[c]) return LTNE_ERR_INVALID_ARG;
   *d = L * sqrt(150.0 * Da / ergun_mean(porosity, n));
   return LTNE_OK;
 }

@@ -56,19 +56,46 @@ __global__ void __launch_bounds__(kHioThreads)
   if (!ok) atomicOr(bad, 1u);
 }
 
-// The porosity plane (compute type) from the host array; bit 0 of *bad set
-// on a value outside (0, 1)
+// The porosity plane (compute type) from the host array, one warp per
+// chunk of kErgunChunk consecutive values (lane l takes values l, l + 32,
+// ...: coalesced reads); bit 0 of *bad set on a value outside (0, 1).  With
+// part, the chunk's Ergun sum in the order ergun_mean takes on the host:
+// each lane's terms in order, then the lanes by strides 16, 8, 4, 2, 1.
+constexpr int kPorWarps = kHioThreads / 32;
+
 template <typename C>
 __global__ void __launch_bounds__(kHioThreads)
     k_porosity_from_host(const double* __restrict__ phi, C* __restrict__ dst, int64_t pitch,
-                         int nx, int ny, uint32_t* __restrict__ bad) {
-  const int x = blockIdx.x * kHioThreads + threadIdx.x;
-  if (x >= nx) return;
+                         int nx, int64_t n, int64_t chunks, double* __restrict__ part,
+                         uint32_t* __restrict__ bad) {
+  static_assert(kErgunLanes == 32, "one warp per chunk");
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * kPorWarps;
   bool ok = true;
-  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
-    const double v = phi[(int64_t)y * nx + x];
-    ok = ok && v > 0.0 && v < 1.0;  // false for NaN too
-    dst[(int64_t)y * pitch + x] = (C)v;
+  for (int64_t c = (int64_t)blockIdx.x * kPorWarps + (threadIdx.x >> 5); c < chunks; c += nwarps) {
+    int64_t i = c * kErgunChunk + lane;
+    int64_t y = i / nx;
+    int64_t x = i - y * nx;
+    double s = 0.0;
+#pragma unroll 8
+    for (int j = 0; j < kErgunPerLane; ++j) {
+      if (i < n) {
+        const double v = phi[i];
+        ok = ok && v > 0.0 && v < 1.0;  // false for NaN too
+        dst[y * pitch + x] = (C)v;
+        if (part) s += ergun_term(v);
+      }
+      i += kErgunLanes;
+      x += kErgunLanes;
+      while (x >= nx) {
+        x -= nx;
+        ++y;
+      }
+    }
+    if (part) {  // uniform over the warp
+      for (int o = kErgunLanes / 2; o >= 1; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) part[c] = s;
+    }
   }
   if (!ok) atomicOr(bad, 1u);
 }
@@ -100,14 +127,15 @@ cudaError_t launch_fields_from_host(void* mac, bool dbl, int64_t plane, int64_t 
 }
 
 cudaError_t launch_porosity_from_host(const double* phi, void* dst, bool dbl, int64_t pitch, int nx,
-                                      int ny, uint32_t* bad, cudaStream_t s) {
-  const dim3 g = hio_grid(nx, ny);
+                                      int ny, double* erg_part, uint32_t* bad, cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny, chunks = ergun_chunks(n);
+  const unsigned blocks = (unsigned)((chunks + kPorWarps - 1) / kPorWarps);
   if (dbl)
-    k_porosity_from_host<double><<<g, kHioThreads, 0, s>>>(phi, static_cast<double*>(dst), pitch,
-                                                           nx, ny, bad);
+    k_porosity_from_host<double><<<blocks, kHioThreads, 0, s>>>(
+        phi, static_cast<double*>(dst), pitch, nx, n, chunks, erg_part, bad);
   else
-    k_porosity_from_host<float><<<g, kHioThreads, 0, s>>>(phi, static_cast<float*>(dst), pitch, nx,
-                                                          ny, bad);
+    k_porosity_from_host<float><<<blocks, kHioThreads, 0, s>>>(
+        phi, static_cast<float*>(dst), pitch, nx, n, chunks, erg_part, bad);
   return cudaGetLastError();
 }
 

@@ -149,11 +149,29 @@ cudaError_t launch_fields_to_host(const void* mac, bool dbl, int64_t plane, int6
                                   int ny, const HostPlanes& hp, cudaStream_t s);
 cudaError_t launch_fields_from_host(void* mac, bool dbl, int64_t plane, int64_t pitch, int nx,
                                     int ny, const HostPlanes& hp, uint32_t* bad, cudaStream_t s);
+// The porosity plane from the caller's host array; with erg_part, also the
+// Ergun chunk sums of the field (kErgunChunk order below) into
+// erg_part[0 .. ergun_chunks(n)).
 cudaError_t launch_porosity_from_host(const double* phi, void* dst, bool dbl, int64_t pitch, int nx,
-                                      int ny, uint32_t* bad, cudaStream_t s);
-// Mean of phi^3 / (1 - phi)^2 over n porosities, summed in a fixed order
-// (the Ergun particle diameter follows from it).
+                                      int ny, double* erg_part, uint32_t* bad, cudaStream_t s);
+
+// The Ergun mean of a porosity field, mean(phi^3 / (1 - phi)^2): with the
+// Ergun permeability (Eq. 7) it fixes the particle diameter that makes the
+// mean of K / L^2 equal to Da.  Its summation order is the same on the host
+// (ergun_mean) and in the porosity kernel, so the diameter has the same bits
+// whichever forms it: chunks of kErgunChunk consecutive values; in chunk c,
+// lane l adds the terms of values c * kErgunChunk + kErgunLanes * j + l for
+// j = 0, 1, ... in order; the lane sums combine by strides 16, 8, 4, 2, 1
+// (sum l += sum l + stride); the chunk sums are added in order.
+constexpr int kErgunLanes = 32, kErgunPerLane = 64, kErgunChunk = kErgunLanes * kErgunPerLane;
+__host__ __device__ inline double ergun_term(double ph) {
+  return ph * ph * ph / ((1.0 - ph) * (1.0 - ph));
+}
+inline int64_t ergun_chunks(int64_t n) { return (n + kErgunChunk - 1) / kErgunChunk; }
+// Mean of phi^3 / (1 - phi)^2 over n porosities, in the order above.
 double ergun_mean(const double* porosity, int64_t n);
+// The same mean from the chunk sums.
+double ergun_mean_of_chunks(const double* part, int64_t n);
 
 // Host-side parameter mapping and observables (ltne_api.cu), shared with
 // the batched form.
