@@ -169,9 +169,13 @@ size_t ltne_workspace_bytes(const ltne_handle* h);
 int ltne_bind_workspace(ltne_handle* h, void* device_ptr, size_t bytes);
 
 /* Initial state S_0: equilibria of the given fields (Eqs. 24, 50, 51) at
-   every node, walls included.  porosity must be non-NULL iff
-   porosity_field was set (values in (0,1)); rho, ux, uy, T_f, T_s may be
-   NULL (defaults rho = 1, u = 0, T = T_ref).  Resets the step counter. */
+   every node, walls included.  Host arrays of nx*ny doubles, row-major:
+   porosity must be non-NULL iff porosity_field was set (values in (0,1));
+   rho, ux, uy, T_f, T_s may be NULL (defaults rho = 1, u = 0, T = T_ref).
+   Resets the step counter.  The arrays are read before the call returns
+   (the device work after them may still be in flight).  INVALID_ARG for a
+   porosity outside (0, 1) or a value that is not finite; the handle then
+   has no fields (STATE) until a call succeeds. */
 int ltne_set_fields(ltne_handle* h, const double* porosity, const double* rho,
                     const double* ux, const double* uy, const double* T_f,
                     const double* T_s);
