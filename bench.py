@@ -56,6 +56,9 @@ def parse():
                     help="nodes per thread of the step kernel (0: the library default)")
     ap.add_argument("--block", default="",
                     help="block shape bx,by of the step kernel (default: the library's)")
+    ap.add_argument("--staging", type=int, default=-1, choices=[-1, 0, 1],
+                    help="two-node step fed from TMA-staged shared-memory tiles (1) or by "
+                         "direct loads (0; -1: the library's default)")
     ap.add_argument("--cavities", type=int, default=256,
                     help="c3: number of cavities (the workload has 256; fewer for profiling)")
     ap.add_argument("--batch-schedule", default="",
@@ -918,6 +921,8 @@ def main():
         else:  # the library's two-node block shape for this storage (128 x 1 for FP32)
             bx, by = cav.schedule[:2] if cav.schedule[2] >= 2 else (128, 1)
         cav.set_schedule(bx, by, args.npt or cav.schedule[2])
+    if args.staging >= 0:
+        cav.set_staging(args.staging)
     schedule = cav.schedule
     cav.set_fields(porosity=phi)
 
