@@ -665,9 +665,10 @@ int set_fields_impl(ltne_handle* h, const double* porosity, const double* rho, c
   const ltne_params& p = h->p;
   if ((porosity != nullptr) != (p.porosity_field != 0)) return LTNE_ERR_INVALID_ARG;
   // The constants are checked before any device work; with a porosity field
-  // the Ergun diameter waits for the staging pass below, which checks and
-  // converts the field and forms the Ergun mean in one read of it (any
-  // positive mean derives the same constants but the diameter).
+  // the Ergun diameter waits until the field has been read below (its mean
+  // formed by the porosity kernel in the direct form, on the host in the
+  // staged one; any positive mean derives the same constants but the
+  // diameter).
   const double any_mean = 1.0;
   int rc = derive(h, porosity ? &any_mean : nullptr);
   if (rc != LTNE_OK) return rc;
