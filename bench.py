@@ -12,9 +12,10 @@ walls.  MLUPS = nodes x steps / seconds.
 Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
 cavity (independent replicas, weak scaling) and rank 0 prints.  At N = 1 the
 line also carries, under "forms", compact runs of the other forms next to
-the plain FP32 kernel: the 256-cavity batch (autotuned schedule), the
-forward + adjoint at 256 x 256 and the FP32 / FP16 / BF16 storage forms at
-8192 x 8192, each with its MLUPS, roofline fraction, errors against the
+the plain FP32 kernel: the same cavity at 1024 x 1024, the 256-cavity batch
+(autotuned schedule), the forward + adjoint at 256 x 256 and the FP32 /
+FP16 / BF16 storage forms at 8192 x 8192, each with its MLUPS, roofline
+fraction, errors against the
 oracle (whose timed run of the checked sample is that leg's CPU baseline)
 and the clocks sampled while it was timed (--no-forms skips them).
 """
@@ -447,6 +448,39 @@ def form_adjoint(stream, peak, gpu):
                              "kind": "oracle (complex step)",
                              "sample": "%d complex-step runs of the 20x16 cavity, 120 steps "
                                        "(%.1f s)" % (len(ref), t_orc)},
+            "clocks": clocks}
+
+
+def form_plain_1024(stream, peak, gpu, steps=2000, warmup=500):
+    """Compact leg of the throughput configuration at its smaller size:
+    the 1024 x 1024 FP32 cavity with per-node porosity (seed 2, Ergun K at
+    mean Da 1e-3, Ra 1e6, H 100, gamma_sf 10), default schedule, 500 warm-up
+    and 2000 timed steps (two population buffers of 80 MB each, more than
+    the L2 together but partly resident in it from step to step)."""
+    import torch
+
+    from paper_1608_04118_gb300.ltne import Cavity, LTNE_K_ERGUN
+
+    c = W.C2_THROUGHPUT
+    n = 1024
+    kw = {k: c[k] for k in ("Ra", "Pr", "Da", "H", "gamma_sf", "sigma", "T_hot", "T_cold",
+                            "T_ref")}
+    phi = W.porosity_field(n, n, c["phi_lo"], c["phi_hi"], c["seed"]).reshape(-1)
+    cav = Cavity(n, n, stream=stream, storage="f32", permeability=LTNE_K_ERGUN,
+                 porosity_field=1, **kw).set_fields(porosity=phi)
+    with torch.cuda.stream(stream):
+        cav.step(warmup)
+    l0 = cav.launches
+    t, clocks = _events_time(stream, lambda: cav.step(steps), gpu)
+    launches = int(cav.launches - l0)
+    rate = n * n * steps / t / 1e6
+    sched = list(cav.schedule)
+    cav.close()
+    achieved = BYTES_PER_LUP["f32"] * rate * 1e6 / 1e9
+    return {"mlups": rate, "lattice": "%dx%d" % (n, n), "steps": steps, "warmup": warmup,
+            "schedule": sched, "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "bytes_per_lup": BYTES_PER_LUP["f32"]},
             "clocks": clocks}
 
 
@@ -1038,7 +1072,8 @@ def main():
         del cav
         torch.cuda.empty_cache()
         gpu = None if args.no_clocks else local
-        forms = {"batched_256_cavities": form_batched(stream, value, peak, gpu),
+        forms = {"plain_fp32_1024": form_plain_1024(stream, peak, gpu),
+                 "batched_256_cavities": form_batched(stream, value, peak, gpu),
                  "adjoint_256": form_adjoint(stream, peak, gpu),
                  "reduced_storage_8192": form_reduced(stream, value, peak, gpu)}
     line = {
