@@ -215,3 +215,54 @@ def test_option_validation_without_gpu(lt):
         assert lib.ltne_step_slabs(h, 2, 1, None, 0) in (
             lt.LTNE_ERR_STATE if supported else lt.LTNE_ERR_INVALID_ARG,)
         lt.ltne_destroy(h)
+
+
+def _ergun_diameter_in_the_documented_order(phi, L, Da):
+    """The Ergun mean's summation order as include/ltne.h and the library
+    state it, restated with Python floats (IEEE doubles): chunks of 2048
+    values, 32 lane sums per chunk (lane l takes values l, l + 32, ... in
+    order), the lane sums combined by strides 16, 8, 4, 2, 1, the chunk
+    sums added in order."""
+    import math
+
+    n = phi.size
+    chunks = []
+    for c in range((n + 2047) // 2048):
+        v = []
+        for lane in range(32):
+            s = 0.0
+            for j in range(64):
+                i = c * 2048 + 32 * j + lane
+                if i < n:
+                    ph = float(phi[i])
+                    s += ph * ph * ph / ((1.0 - ph) * (1.0 - ph))
+            v.append(s)
+        st = 16
+        while st >= 1:
+            for lane in range(st):
+                v[lane] = v[lane] + v[lane + st]
+            st //= 2
+        chunks.append(v[0])
+    acc = 0.0
+    for x in chunks:
+        acc += x
+    return L * math.sqrt(150.0 * Da / (acc / n))
+
+
+def test_ergun_diameter_follows_its_documented_order():
+    """ltne_ergun_diameter (host code, no device) gives the bits of the
+    documented summation order -- the order the device's porosity kernel
+    also takes -- and the oracle's diameter to rounding."""
+    from oracle import ergun_diameter
+    from paper_1608_04118_gb300 import ltne as lt
+    from paper_1608_04118_gb300 import workloads as W
+
+    for nx, ny, seed in ((100, 50, 3), (64, 32, 4), (7, 5, 5)):
+        phi = W.porosity_field(nx, ny, 0.3, 0.9, seed).reshape(-1)
+        d = lt.ltne_ergun_diameter(phi, ny - 1, 1e-3)
+        assert d == _ergun_diameter_in_the_documented_order(phi, ny - 1, 1e-3), (nx, ny)
+        assert d == pytest.approx(ergun_diameter(phi, ny - 1, 1e-3), rel=1e-14)
+    bad = W.porosity_field(10, 10, 0.3, 0.9, 6).reshape(-1)
+    bad[57] = 1.0
+    with pytest.raises(lt.LtneError):
+        lt.ltne_ergun_diameter(bad, 9, 1e-3)
