@@ -254,6 +254,14 @@ __global__ void __launch_bounds__(256, (kCapped && sizeof(C) == 4) ? 4 : 1)
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int64_t off = (int64_t)y * pitch + x;
+  // one-wave build: this node's gradient accumulators, read here so that
+  // their latency is not the last link of the chain below (the capped build
+  // keeps its registers for the chain and reads them at the end)
+  C phib0 = C(0), hb0 = C(0);
+  if (!kCapped) {
+    phib0 = phib[off];
+    hb0 = hb[off];
+  }
   // the next reverse step's state, recomputed a whole segment ago and mostly
   // evicted to HBM by now: fetched into L2 while this step runs (one-wave
   // build only: on larger lattices, bound by HBM throughput, it cost 4 %)
@@ -296,8 +304,12 @@ __global__ void __launch_bounds__(256, (kCapped && sizeof(C) == 4) ? 4 : 1)
   else
     store19(lam_out, plane, off, fb, gfb, gsb);
   medium_adjoint<C>(P, ph, md, mdb, pb, hv);
-  phib[off] += pb;
-  hb[off] += hv;
+  if (kCapped) {
+    phib0 = phib[off];
+    hb0 = hb[off];
+  }
+  phib[off] = phib0 + pb;
+  hb[off] = hb0 + hv;
 }
 
 // The folds' porosity terms, kept in their wall nodes' places, added to the
